@@ -1,0 +1,282 @@
+"""FP64 CPU oracle for the light-field-probe ray tracer -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline /
+reference arm may import this package. The product path (the C-ABI library
+and its Python binding) never imports it and shares no code with it.
+
+The arithmetic lives in ``lfp_oracle.c`` (double precision, one pixel at a
+time, OpenMP over pixels); this module only marshals numpy arrays. Every
+function cites the passage of Liu, Nowrouzezahrai & McGuire, "Real-Time Scene
+Reconstruction using Light Field Probes" (arXiv 2507.14624) that it follows;
+the C file's header lists the readings taken where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lfp_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+
+MISS, HIT, UNKNOWN = 0, 1, 2
+MARCH_FLAT, MARCH_HIER, MARCH_HIER_SHORTCUT = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction: same results on x86-64 and aarch64)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared",
+                        "-fPIC", "-o", _LIB + ".tmp", _SRC, "-lm"], check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("origin", ctypes.c_double * 3), ("spacing", ctypes.c_double),
+                ("N", ctypes.c_int), ("M", ctypes.c_int),
+                ("thickness_rel", ctypes.c_double), ("eye_eps", ctypes.c_double),
+                ("march_mode", ctypes.c_int)]
+
+
+class _Probes(ctypes.Structure):
+    _fields_ = [("dist", ctypes.c_void_p), ("normal", ctypes.c_void_p), ("radiance", ctypes.c_void_p),
+                ("mip_min", ctypes.c_void_p), ("mip_max", ctypes.c_void_p)]
+
+
+class _View(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_double * 3), ("right", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("fwd", ctypes.c_double * 3), ("fov_y", ctypes.c_double), ("W", ctypes.c_int),
+                ("H", ctypes.c_int)]
+
+
+class _Cell(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_int * 3), ("t_in", ctypes.c_double), ("t_out", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        vp, ll, i, d = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_double
+        G, Pr, V = ctypes.POINTER(_Grid), ctypes.POINTER(_Probes), ctypes.POINTER(_View)
+        sig = {
+            "orc_oct_encode_n": ([ll, vp, vp], None),
+            "orc_oct_decode_n": ([ll, vp, vp], None),
+            "orc_mirror_texel": ([i, vp, vp], None),
+            "orc_build_mip": ([i, i, i, vp, vp, vp], None),
+            "orc_split_segments": ([vp, vp, vp, d, d, vp], i),
+            "orc_grid_cells": ([G, vp, vp, vp, i], i),
+            "orc_cage_order": ([G, vp, vp, vp], None),
+            "orc_render": ([G, Pr, V, ll, vp, vp, vp, vp, vp, vp, vp, vp], None),
+            "orc_trace_rays": ([G, Pr, ll, vp, vp, vp, vp, vp, vp, vp, vp], None),
+            "orc_trace_one_probe": ([G, Pr, i, vp, vp, d, d, vp, vp, vp], i),
+            "orc_walk_segment": ([vp, vp, d, d, i, i, vp, vp], i),
+            "orc_backward": ([G, ll, vp, vp, vp, vp, vp], None),
+            "orc_bilinear_taps": ([i, vp, vp, vp, vp], None),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+# ---------------------------------------------------------------------------
+# octahedral map (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def oct_encode(d: np.ndarray) -> np.ndarray:
+    """Direction(s) [..., 3] -> octahedral square point(s) [..., 2] in [-1, 1]^2."""
+    d = _f64(d)
+    shp = d.shape[:-1]
+    d = d.reshape(-1, 3)
+    out = np.empty((len(d), 2), np.float64)
+    _load().orc_oct_encode_n(len(d), _p(d), _p(out))
+    return out.reshape(*shp, 2)
+
+
+def oct_decode(p: np.ndarray) -> np.ndarray:
+    """Octahedral square point(s) [..., 2] -> unit direction(s) [..., 3]."""
+    p = _f64(p)
+    shp = p.shape[:-1]
+    p = p.reshape(-1, 2)
+    out = np.empty((len(p), 3), np.float64)
+    _load().orc_oct_decode_n(len(p), _p(p), _p(out))
+    return out.reshape(*shp, 3)
+
+
+def mirror_texel(R: int, i: int, j: int):
+    ci, cj = ctypes.c_int(i), ctypes.c_int(j)
+    _load().orc_mirror_texel(R, ctypes.byref(ci), ctypes.byref(cj))
+    return ci.value, cj.value
+
+
+def bilinear_taps(N: int, uv):
+    uv = _f64(uv)
+    ti = np.empty(4, np.int32)
+    tj = np.empty(4, np.int32)
+    w = np.empty(4, np.float64)
+    _load().orc_bilinear_taps(N, _p(uv), _p(ti), _p(tj), _p(w))
+    return ti, tj, w
+
+
+def build_mip(dist: np.ndarray, M: int):
+    """Per-block min and max of the distance maps (low-resolution map, Sec. 5.1)."""
+    dist = np.ascontiguousarray(dist, np.float32)
+    P, N, _ = dist.shape
+    mn = np.empty((P, M, M), np.float32)
+    mx = np.empty((P, M, M), np.float32)
+    _load().orc_build_mip(P, N, M, _p(dist), _p(mn), _p(mx))
+    return mn, mx
+
+
+def split_segments(X, w, O, t0, t1):
+    b = np.empty(5, np.float64)
+    n = _load().orc_split_segments(_p(_f64(X)), _p(_f64(w)), _p(_f64(O)), t0, t1, _p(b))
+    return [(b[k], b[k + 1]) for k in range(n)]
+
+
+def walk_segment(Y0, w, ta, tb, R, max_texels=100000):
+    """Texels (i, j) and their t-intervals along one octant segment at resolution R."""
+    ij = np.empty((max_texels, 2), np.int32)
+    tt = np.empty((max_texels, 2), np.float64)
+    n = _load().orc_walk_segment(_p(_f64(Y0)), _p(_f64(w)), ta, tb, R, max_texels, _p(ij), _p(tt))
+    return ij[:n].copy(), tt[:n].copy()
+
+
+# ---------------------------------------------------------------------------
+# the tracer
+# ---------------------------------------------------------------------------
+
+class Oracle:
+    """FP64 tracer over one probe grid.
+
+    grid: an object with nx, ny, nz, origin, spacing, N, M (e.g. synth.Grid).
+    dist [P][N][N], normal [P][N][N][3], radiance [P][N][N][3]: float32 maps.
+    """
+
+    def __init__(self, grid, dist, normal, radiance, thickness_rel=1.0, eye_eps=None,
+                 march=MARCH_HIER):
+        self.grid = grid
+        self.dist = np.ascontiguousarray(dist, np.float32)
+        self.normal = np.ascontiguousarray(normal, np.float32)
+        self.radiance = np.ascontiguousarray(radiance, np.float32)
+        self.mip_min, self.mip_max = build_mip(self.dist, grid.M)
+        self.thickness_rel = float(thickness_rel)
+        self.eye_eps = float(1e-6 * grid.spacing if eye_eps is None else eye_eps)
+        self.march = march
+
+    def _g(self, march=None):
+        g = _Grid()
+        g.nx, g.ny, g.nz = self.grid.nx, self.grid.ny, self.grid.nz
+        for a in range(3):
+            g.origin[a] = float(self.grid.origin[a])
+        g.spacing = float(self.grid.spacing)
+        g.N, g.M = self.grid.N, self.grid.M
+        g.thickness_rel = self.thickness_rel
+        g.eye_eps = self.eye_eps
+        g.march_mode = self.march if march is None else march
+        return g
+
+    def _pr(self):
+        pr = _Probes()
+        pr.dist, pr.normal, pr.radiance = (self.dist.ctypes.data, self.normal.ctypes.data,
+                                           self.radiance.ctypes.data)
+        pr.mip_min, pr.mip_max = self.mip_min.ctypes.data, self.mip_max.ctypes.data
+        return pr
+
+    @staticmethod
+    def _v(view):
+        v = _View()
+        for a in range(3):
+            v.pos[a], v.right[a], v.up[a], v.fwd[a] = view.pos[a], view.right[a], view.up[a], view.fwd[a]
+        v.fov_y, v.W, v.H = view.fov_y, view.W, view.H
+        return v
+
+    def render(self, view, pixels=None, march=None, counters=False):
+        """Trace the listed pixels (flat indices y*W + x; all when None) of one view.
+
+        Returns a dict: rgb [n,3] f64, cls [n] u8, probe [n] i32, uv [n,2] f64,
+        texel [n,2] i32 (fine texel that decided the HIT), t_hit [n] f64 and,
+        when asked, counters [n,5] (coarse, fine, normal fetches, cells, probes).
+        """
+        if pixels is None:
+            n = view.W * view.H
+            pix = None
+        else:
+            pix = np.ascontiguousarray(pixels, np.int64)
+            n = len(pix)
+        out = {"rgb": np.zeros((n, 3)), "cls": np.zeros(n, np.uint8), "probe": np.zeros(n, np.int32),
+               "uv": np.zeros((n, 2)), "texel": np.zeros((n, 2), np.int32), "t_hit": np.zeros(n)}
+        cnt = np.zeros((n, 5), np.int64) if counters else None
+        g, pr, v = self._g(march), self._pr(), self._v(view)
+        _load().orc_render(ctypes.byref(g), ctypes.byref(pr), ctypes.byref(v), n, _p(pix),
+                           _p(out["rgb"]), _p(out["cls"]), _p(out["probe"]), _p(out["uv"]),
+                           _p(out["texel"]), _p(out["t_hit"]), _p(cnt))
+        if counters:
+            out["counters"] = cnt
+        return out
+
+    def trace_rays(self, X, W, march=None):
+        """Trace arbitrary rays: origins X [n,3], directions W [n,3]."""
+        X = _f64(X).reshape(-1, 3)
+        W = _f64(W).reshape(-1, 3)
+        n = len(X)
+        out = {"rgb": np.zeros((n, 3)), "cls": np.zeros(n, np.uint8), "probe": np.zeros(n, np.int32),
+               "uv": np.zeros((n, 2)), "texel": np.zeros((n, 2), np.int32), "t_hit": np.zeros(n)}
+        g, pr = self._g(march), self._pr()
+        _load().orc_trace_rays(ctypes.byref(g), ctypes.byref(pr), n, _p(X), _p(W), _p(out["rgb"]),
+                               _p(out["cls"]), _p(out["probe"]), _p(out["uv"]), _p(out["texel"]),
+                               _p(out["t_hit"]))
+        return out
+
+    def trace_one_probe(self, probe, X, w, t0, t1, march=None):
+        """traceOneProbe over [t0, t1] (Appendix A): (class, texel, uv, t_hit)."""
+        g, pr = self._g(march), self._pr()
+        tex = np.empty(2, np.int32)
+        uv = np.empty(2, np.float64)
+        th = ctypes.c_double()
+        c = _load().orc_trace_one_probe(ctypes.byref(g), ctypes.byref(pr), probe, _p(_f64(X)), _p(_f64(w)),
+                                        t0, t1, _p(tex), _p(uv), ctypes.byref(th))
+        return c, tex, uv, th.value
+
+    def grid_cells(self, X, w, max_cells=1024):
+        """Grid iterator (Sec. 4.3): [(cell ijk, t_in, t_out)] in ray order."""
+        cells = (_Cell * max_cells)()
+        n = _load().orc_grid_cells(ctypes.byref(self._g()), _p(_f64(X)), _p(_f64(w)), cells, max_cells)
+        return [(tuple(cells[k].c), cells[k].t_in, cells[k].t_out) for k in range(n)]
+
+    def cage_order(self, c, P):
+        order = np.empty(8, np.int32)
+        _load().orc_cage_order(ctypes.byref(self._g()), _p(np.asarray(c, np.int32)), _p(_f64(P)), _p(order))
+        return order
+
+    def backward(self, grad_rgb, cls, probe, uv):
+        """Adjoint of render w.r.t. radiance: [P][N][N][3] f64 (sum over pixels)."""
+        P, N = self.dist.shape[0], self.grid.N
+        grad = np.zeros((P, N, N, 3), np.float64)
+        g = _f64(grad_rgb).reshape(-1, 3)
+        c = np.ascontiguousarray(cls, np.uint8)
+        pb = np.ascontiguousarray(probe, np.int32)
+        uv = _f64(uv).reshape(-1, 2)
+        _load().orc_backward(ctypes.byref(self._g()), len(c), _p(g), _p(c), _p(pb), _p(uv), _p(grad))
+        return grad
