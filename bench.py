@@ -1,0 +1,350 @@
+"""Benchmark: forward render throughput of the light-field-probe tracer.
+
+Default workload: the room-scale grid (4x4x4 probes at spacing 0.5, 256x256
+FP32 maps, 16x16 min/max map) rendering one 1920x1080 view at 70 deg, the
+configuration the headline metric (Mrays/s at 1080p) is quoted on. One step is
+one forward render of that view; inputs (probe maps, camera) are resident in
+HBM when the timed region starts, and L2 is flushed (a 256 MiB write) before
+every timed step, outside the timed kernel.
+
+Also reported: e2e (the same metric through the C ABI with host output
+buffers, copies inside the timed region), the roofline of the render kernel
+(algorithmic bytes from the kernel's own fetch counters), the FP64 oracle on
+the host cores (cpu_baseline), fwd+adjoint ms/view on the differentiable-fit
+views, and SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lfp|reference]
+                  [--workload room|batched]
+Under torchrun every rank renders its own copy of the workload (weak scaling,
+no collective on the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s at 1080p (fwd) and fwd+adjoint ms/view; % of HBM/L2 roofline"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lfp", choices=["lfp", "reference"])
+    ap.add_argument("--workload", default="room", choices=["room", "batched"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_info(name, views, grid):
+    if name == "room":
+        desc = "room: 4x4x4 probes spacing 0.5, N=256 M=16, FP32 texels, 64 spheres + 16 boxes, 1 view 1920x1080 70deg"
+    else:
+        desc = ("batched: 8x8x4 probes spacing 0.5, N=512 M=32, FP16 radiance+normal, 256 spheres + 64 boxes, "
+                "32 views 640x480..3840x2160 on a Catmull-Rom path, persistent launch")
+    return {"workload": desc, "views": len(views), "rays_per_step": int(sum(v.W * v.H for v in views)),
+            "probes": grid.n_probes, "N": grid.N, "M": grid.M, "l2": "flushed before every timed step (256 MiB write)"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def render_source_sha():
+    h = hashlib.sha256()
+    for f in ("render.cu", "lfp_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2507_14624_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the render kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", f"render_{workload}_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("source_sha") == render_source_sha():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def build_workload(name):
+    import synth
+    sc, views = synth.workload(name)
+    d, n, r = sc.probe_maps()
+    return sc, views, d, n, r
+
+
+def bytes_model(c, rad_fmt_f16, nrm_fmt_f16):
+    """Algorithmic bytes of one launch from the kernel's fetch counters:
+    8 per low-res texel (min, max), 4 per full-res distance texel, 8 / 4 per
+    normal (FP32 / FP16 octahedral pair), 12 / 8 per radiance tap, and 13 per
+    ray written (rgb f32 + class u8)."""
+    s_n = 4 if nrm_fmt_f16 else 8
+    s_r = 8 if rad_fmt_f16 else 12
+    return 8 * c["coarse"] + 4 * c["fine"] + s_n * c["normal"] + s_r * c["radiance"] + 13 * c["rays"]
+
+
+def run_lfp(args):
+    import torch
+    import paper_2507_14624_gb300 as lfpk
+    from paper_2507_14624_gb300 import lfp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sc, views, d, n, r = build_workload(args.workload)
+    f16 = args.workload == "batched"
+    fmt = lfpk.LFP_TEXEL_F16 if f16 else lfpk.LFP_TEXEL_F32
+    grid = lfpk.ProbeGrid(sc.grid, radiance_fmt=fmt, normal_fmt=fmt)
+    grid.upload(d, n, r)
+    sched = lfpk.LFP_SCHED_PERSISTENT if len(views) > 1 else 0
+    arr, nv, total = lfpk.make_views(views)
+    dev = torch.device("cuda", local)
+    rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
+    cls = torch.empty(total, dtype=torch.uint8, device=dev)
+    outs = lfp.lfp_outputs()
+    outs.rgb, outs.cls = rgb.data_ptr(), cls.data_ptr()
+    opts = lfp.lfp_render_opts()
+    opts.schedule = sched
+    stream = torch.cuda.current_stream()
+    sh = lfpk._stream_handle(stream)
+    launches_per_step = (nv + 127) // 128
+
+    def step():
+        lfp.lfp_render_ex(grid.handle, arr, nv, outs, opts, sh)
+
+    # fetch counters of one launch (untimed; counting variant of the kernel)
+    cnt = torch.zeros(lfp.N_COUNTERS, dtype=torch.int64, device=dev)
+    oc = lfp.lfp_outputs()
+    oc.rgb, oc.cls, oc.counters = rgb.data_ptr(), cls.data_ptr(), cnt.data_ptr()
+    lfp.lfp_render_ex(grid.handle, arr, nv, oc, opts, sh)
+    torch.cuda.synchronize()
+    counters = dict(zip(lfp.COUNTER_NAMES, (int(x) for x in cnt.cpu().tolist())))
+    alg_bytes = bytes_model(counters, f16, f16)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]  # ms, render kernel only
+    t_sum = sum(times) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_sum], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_sum = tt.item()
+    rays = total * args.steps * world
+    value = rays / t_sum / 1e6
+    ms_launch = sum(times) / len(times)
+
+    # e2e through the C ABI: host output buffers, copies inside the timed region
+    rgb_h = torch.empty((total, 3), dtype=torch.float32).pin_memory()
+    cls_h = torch.empty(total, dtype=torch.uint8).pin_memory()
+    grid.render_to_host(views, rgb_h, cls_h)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        grid.render_to_host(views, rgb_h, cls_h)
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": round(total * e2e_steps * world / e2e_t / 1e6, 3), "unit": "Mrays/s",
+           "h2d_bytes_per_step": int(nv * 72), "d2h_bytes_per_step": int(total * 13)}
+
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (ms_launch / 1e3) / 1e9
+    traffic = ncu_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": "render_kernel",
+                "counters_per_launch": counters}
+
+    extra = {}
+    if not args.no_adjoint and rank == 0:
+        extra["fwd_adj_ms_per_view"] = fwd_adjoint_ms_per_view(torch, lfpk, dev)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(sc, views, d, n, r, budget_s=10.0)
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_launch, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f16+f32" if f16 else "f32", "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
+                "config": workload_info(args.workload, views, sc.grid), "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "roofline": roofline, "clocks": clk,
+                "cpu_baseline": cpu, **extra}
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def fwd_adjoint_ms_per_view(torch, lfpk, dev, steps=5):
+    """Differentiable-fit workload: the room grid (seed 4), 64 views of
+    800x800; one step = batched forward with saved state + adjoint scatter
+    into radiance gradients. Reported per view."""
+    import synth
+    sc, views = synth.workload("fit")
+    d, n, r = sc.probe_maps()
+    g = lfpk.ProbeGrid(sc.grid)
+    g.upload(d, n, r)
+    out = g.render(views, aux=True, schedule=lfpk.LFP_SCHED_PERSISTENT)
+    grad_rgb = torch.randn_like(out["rgb"])
+    grad = torch.zeros((g.n_probes, g.N, g.N, 3), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        out = g.render(views, aux=True, schedule=lfpk.LFP_SCHED_PERSISTENT)
+        g.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        out = g.render(views, aux=True, schedule=lfpk.LFP_SCHED_PERSISTENT)
+        g.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
+    e1.record()
+    torch.cuda.synchronize()
+    g.close()
+    return round(e0.elapsed_time(e1) / steps / len(views), 4)
+
+
+def cpu_baseline(sc, views, d, n, r, budget_s=10.0, max_reps=10):
+    """The FP64 oracle on the host cores, on the same view: whole frames
+    (every pixel) repeated until ~budget_s of CPU time."""
+    import oracle
+    o = oracle.Oracle(sc.grid, d, n, r)
+    rays, t0, reps = 0, time.perf_counter(), 0
+    while reps < max_reps:
+        for v in views[:1]:
+            o.render(v)
+            rays += v.W * v.H
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(rays / dt / 1e6, 4), "unit": "Mrays/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{reps} full frame(s) of view 0 ({views[0].W}x{views[0].H}), every pixel"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores (there is no other
+    implementation of the method to run); each step renders the full first
+    view of the workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    sc, views, d, n, r = build_workload(args.workload)
+    o = oracle.Oracle(sc.grid, d, n, r)
+    v = views[0]
+    for _ in range(args.warmup):
+        o.render(v, pixels=range(0, v.W * v.H, 64))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.render(v)
+    dt = time.perf_counter() - t0
+    value = v.W * v.H * args.steps / dt / 1e6
+    cpu = {"value": round(value, 4), "unit": "Mrays/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"full frame {v.W}x{v.H} per step"}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mrays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
+            "config": workload_info(args.workload, views, sc.grid), "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_lfp(a)

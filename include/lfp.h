@@ -1,0 +1,212 @@
+/*
+ * lfp.h -- C ABI of the GB300 light-field-probe ray tracer.
+ *
+ * Method: Liu, Nowrouzezahrai & McGuire, "Real-Time Scene Reconstruction
+ * using Light Field Probes" (arXiv 2507.14624). A camera ray (X, w1) is traced
+ * through a uniform 3D grid of probes (Sec. 3, multiple probes; Sec. 4.3 grid
+ * iterator). Each probe stores octahedral maps (Sec. 3, octahedral mapping) of
+ * radial distance, surface normal and radiance, plus a low-resolution distance
+ * map (Sec. 5.1; here a conservative per-block min/max). Per probe the ray is
+ * split at the probe's axis planes into at most 4 segments, marched on the
+ * low-resolution map and then on the full-resolution map, and classified HIT /
+ * MISS / UNKNOWN (Sec. 4.2; Appendix A, traceOneRaySegment,
+ * lowResolutionTracing, highResolutionTracing). UNKNOWN falls through to the
+ * next probe of the 8-probe cage. A HIT is shaded by a bilinear radiance fetch
+ * (Sec. 3: L_o(X, w1) = L_p(w2)).
+ *
+ * Conventions shared by every entry point
+ *   - Octahedral maps are N x N, row-major, row j, column i; texel (i, j)
+ *     holds direction decode(((i + .5) / N * 2 - 1, (j + .5) / N * 2 - 1)),
+ *     pole +z, lower octants unfolded onto the square's corners.
+ *   - Probe index p = ix + nx * (iy + ny * iz); probe p sits at
+ *     origin + spacing * (ix, iy, iz) (float32 arithmetic).
+ *   - Pixel (x, y) of a view (x to the right, y down) is written at flat index
+ *     out_offset + y * W + x of every per-pixel output.
+ *   - Every call that takes a stream is asynchronous on that stream (a
+ *     cudaStream_t passed as void*, NULL = the legacy default stream) unless
+ *     stated otherwise; device pointers must stay valid until the stream has
+ *     executed the call. No call allocates on behalf of the caller's outputs.
+ *   - Every call returns a status; no C++ exception crosses the ABI. A launch
+ *     failure is reported as LFP_ERR_CUDA (checked with cudaGetLastError).
+ *   - The library is not thread-safe per grid: calls on one grid must come
+ *     from one host thread at a time. Distinct grids are independent.
+ */
+#ifndef LFP_H
+#define LFP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LFP_OK = 0,
+    LFP_ERR_INVALID_ARG = 1, /* a pointer, size or descriptor field is invalid */
+    LFP_ERR_OOM = 2,         /* a device allocation failed */
+    LFP_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    LFP_ERR_STATE = 4,       /* call order violated (e.g. render before upload) */
+    LFP_WARN_STEPLIMIT = 100 /* some ray hit the per-ray step cap (class 3) */
+} lfp_status;
+
+typedef enum { LFP_TEXEL_F32 = 0, LFP_TEXEL_F16 = 1 } lfp_texel_fmt;
+
+/* per-pixel classes written to `cls` */
+enum {
+    LFP_CLASS_MISS = 0,      /* the ray left the grid in front of every surface */
+    LFP_CLASS_HIT = 1,       /* a probe saw the intersection (rgb valid) */
+    LFP_CLASS_UNKNOWN = 2,   /* no probe could decide (all UNKNOWN somewhere) */
+    LFP_CLASS_STEPLIMIT = 3  /* max_steps texel visits reached */
+};
+
+/* Grid of probes (Sec. 3 "probes are placed at the vertices of a uniform 3D grid").
+ *   nx, ny, nz >= 2          probes per axis (cells: (nx-1)(ny-1)(nz-1))
+ *   origin, spacing > 0      probe (0,0,0) position and grid pitch
+ *   N                        full-resolution map side, even, 2..8192
+ *   M                        low-resolution map side, even, N % M == 0, M <= N
+ *   radiance_fmt, normal_fmt device storage of radiance (RGB) and normals
+ *                            (octahedral-encoded RG); distance is always float32
+ *   thickness_rel            th: a texel crossing counts while the ray's
+ *                            nearest radial distance is <= d (1 + 4 th / N);
+ *                            th < 0 selects the two-way rule of Appendix A
+ *                            highResolutionTracing (every crossing -> normal test)
+ *   eye_eps                  |X - O| < eye_eps is "eye aligned with a probe"
+ *                            (Sec. 4.2, O(1) lookup); 0 -> 1e-6 * spacing
+ *   max_steps                cap on texel visits per ray, 0 = none */
+typedef struct {
+    int nx, ny, nz;
+    float origin[3];
+    float spacing;
+    int N, M;
+    lfp_texel_fmt radiance_fmt, normal_fmt;
+    float thickness_rel;
+    float eye_eps;
+    int max_steps;
+} lfp_grid_desc;
+
+/* Pinhole camera (the ray (X, w1) of Sec. 3). The ray through pixel (x, y)
+ * starts at pos and runs along normalize(fwd + a right + b up) with
+ * a = ((x + .5) / W * 2 - 1) tan(fov_y / 2) W / H and
+ * b = (1 - (y + .5) / H * 2) tan(fov_y / 2); fov_y is vertical, in radians.
+ * right/up/fwd need not be orthonormal. out_offset: first flat output index. */
+typedef struct {
+    float pos[3], right[3], up[3], fwd[3];
+    float fov_y;
+    int W, H;
+    long long out_offset;
+} lfp_view;
+
+/* Probe maps for `count` consecutive probes, float32, tightly packed:
+ *   dist      [count][N][N]     radial distance from the probe to the nearest surface
+ *   normal    [count][N][N][3]  unit surface normal at that surface point
+ *   radiance  [count][N][N][3]  linear RGB leaving that point towards the probe
+ * is_device: 0 = host pointers (copied), 1 = device pointers (read in place). */
+typedef struct {
+    const float* dist;
+    const float* normal;
+    const float* radiance;
+    int is_device;
+} lfp_probe_planes;
+
+typedef struct lfp_grid lfp_grid;
+
+/* Optional per-pixel outputs and statistics of lfp_render_ex. Any pointer
+ * may be NULL. All device pointers, flat per-pixel arrays (see conventions).
+ *   rgb [P][3] f32, cls [P] u8, aux_probe [P] i32 (-1 unless HIT),
+ *   aux_uv [P][2] f32 (shading coordinate in [0,1]^2, HIT only),
+ *   hit_texel [P] i32: i + N * j of the full-resolution texel that decided
+ *   the HIT (-1 otherwise), counters [8] u64, accumulated (not cleared):
+ *   low-res texel visits, full-res texel visits, normal fetches, radiance
+ *   texel fetches, cells entered, probes traced, HIT pixels, rays. */
+typedef struct {
+    float* rgb;
+    uint8_t* cls;
+    int32_t* aux_probe;
+    float* aux_uv;
+    int32_t* hit_texel;
+    unsigned long long* counters;
+} lfp_outputs;
+
+/* Launch options for lfp_render_ex (zero-initialised = defaults). */
+enum { LFP_MARCH_HIER = 0, LFP_MARCH_FLAT = 1 };
+enum { LFP_SCHED_AUTO = 0, LFP_SCHED_TILES = 1, LFP_SCHED_PERSISTENT = 2 };
+typedef struct {
+    int march;      /* LFP_MARCH_HIER (low-res then full-res) or LFP_MARCH_FLAT
+                       (Appendix A RayMarching over the full-res map only) */
+    int tile_w;     /* ray tile width x height per CTA; 0 = autotuned/default.
+                       Valid shapes: 8x4, 8x8, 16x8, 16x16, 32x8 */
+    int tile_h;
+    int schedule;   /* LFP_SCHED_*: one CTA per tile, or a persistent grid
+                       pulling tiles from a queue */
+} lfp_render_opts;
+
+/* Create a grid; allocates the device planes for all nx*ny*nz probes on the
+ * current device. *out receives the handle (owned by the caller, release with
+ * lfp_destroy_grid). Errors: INVALID_ARG (desc), OOM, CUDA. */
+lfp_status lfp_create_grid(const lfp_grid_desc* desc, lfp_grid** out);
+
+/* Upload maps for probes [first_probe, first_probe + count) and rebuild their
+ * low-resolution min/max maps (Sec. 5.1). Host planes are copied before the
+ * call returns only if the stream is synchronous; otherwise they must stay
+ * valid until the stream has run the copy. Errors: INVALID_ARG, OOM, CUDA. */
+lfp_status lfp_upload_probes(lfp_grid* grid, int first_probe, int count,
+                             const lfp_probe_planes* planes, void* cuda_stream);
+
+/* Render n_views views (Sec. 3 problem statement; Sec. 4.2-4.3; Appendix A).
+ * `views` is host memory, read before the call returns. rgb [P][3] f32 and
+ * cls [P] u8 are required; aux_probe [P] i32 and aux_uv [P][2] f32 are the
+ * saved state for lfp_render_backward and may be NULL. Pixels that are not
+ * HIT get rgb 0. Returns LFP_ERR_STATE if any probe was never uploaded. */
+lfp_status lfp_render(lfp_grid* grid, const lfp_view* views, int n_views,
+                      float* rgb, uint8_t* cls, int32_t* aux_probe, float* aux_uv,
+                      void* cuda_stream);
+
+/* lfp_render with optional outputs and launch options (opts may be NULL). */
+lfp_status lfp_render_ex(lfp_grid* grid, const lfp_view* views, int n_views,
+                         const lfp_outputs* out, const lfp_render_opts* opts,
+                         void* cuda_stream);
+
+/* Render into HOST memory: one call that runs lfp_render on device buffers
+ * owned by the grid and copies rgb [P][3] f32 and cls [P] u8 back, then
+ * synchronises the stream. rgb_host / cls_host: host memory (pinned memory
+ * gives asynchronous copies), either may be NULL. */
+lfp_status lfp_render_to_host(lfp_grid* grid, const lfp_view* views, int n_views,
+                              float* rgb_host, uint8_t* cls_host, void* cuda_stream);
+
+/* Adjoint of lfp_render with respect to radiance (the paper has no adjoint;
+ * it follows from L_o(X, w1) = L_p(w2): for fixed distance and normal maps
+ * the HIT texel and bilinear weights do not depend on radiance, so
+ * d rgb_c / d radiance[p, texel_k, c] = w_k). For each HIT pixel, adds
+ * w_k * grad_rgb[c] into grad_radiance [P_total][N][N][3] f32 (device,
+ * ACCUMULATED: the caller zeroes it). cls, aux_probe, aux_uv: the forward's
+ * outputs for the same views; the grid must not have changed in between
+ * except through lfp_set_radiance. */
+lfp_status lfp_render_backward(lfp_grid* grid, const lfp_view* views, int n_views,
+                               const float* grad_rgb, const uint8_t* cls,
+                               const int32_t* aux_probe, const float* aux_uv,
+                               float* grad_radiance, void* cuda_stream);
+
+/* Replace every probe's radiance from a device array [P_total][N][N][3] f32
+ * (the fitted parameters); converted to the grid's radiance format. */
+lfp_status lfp_set_radiance(lfp_grid* grid, const float* dev_radiance_f32, void* cuda_stream);
+
+/* Synchronise the stream and report (then clear) the device flag word:
+ * LFP_WARN_STEPLIMIT if some ray reached max_steps since the last call. */
+lfp_status lfp_check_flags(lfp_grid* grid, void* cuda_stream);
+
+/* Device bytes the grid's probe storage takes for a descriptor (maps + mip),
+ * the byte accounting of Sec. 6 (memory efficient representation). */
+lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes);
+
+/* Release a grid (NULL-safe; synchronises the device first). */
+void lfp_destroy_grid(lfp_grid* grid);
+
+/* Static string for a status code. */
+const char* lfp_status_string(lfp_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LFP_H */

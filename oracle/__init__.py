@@ -82,6 +82,7 @@ def _load():
             "orc_walk_segment": ([vp, vp, d, d, i, i, vp, vp], i),
             "orc_backward": ([G, ll, vp, vp, vp, vp, vp], None),
             "orc_bilinear_taps": ([i, vp, vp, vp, vp], None),
+            "orc_num_threads": ([], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -122,6 +123,11 @@ def oct_decode(p: np.ndarray) -> np.ndarray:
     out = np.empty((len(p), 3), np.float64)
     _load().orc_oct_decode_n(len(p), _p(p), _p(out))
     return out.reshape(*shp, 3)
+
+
+def num_threads() -> int:
+    """Host threads the oracle's OpenMP loops use."""
+    return int(_load().orc_num_threads())
 
 
 def mirror_texel(R: int, i: int, j: int):

@@ -771,3 +771,15 @@ void orc_backward(const orc_grid* g, long long n_pix, const double* grad_rgb,
 void orc_bilinear_taps(int N, const double* uv, int* ti, int* tj, double* w) {
     bilinear_taps(N, uv, ti, tj, w);
 }
+
+/* threads the OpenMP loops above run on (reported with CPU timings) */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,195 @@
+"""GB300 light-field-probe ray tracer (Liu, Nowrouzezahrai & McGuire, arXiv 2507.14624).
+
+``lfp`` is the ctypes binding of the C ABI (include/lfp.h). This module adds a
+thin torch-facing layer: device buffers are torch tensors, streams are torch
+streams, and ``render`` is differentiable with respect to probe radiance
+through the hand-written adjoint kernel. Nothing here computes any step of the
+tracer; it only allocates, marshals arguments and calls the library.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import lfp
+from .lfp import (LFP_CLASS_HIT, LFP_CLASS_MISS, LFP_CLASS_STEPLIMIT, LFP_CLASS_UNKNOWN, LFP_MARCH_FLAT,
+                  LFP_MARCH_HIER, LFP_SCHED_PERSISTENT, LFP_SCHED_TILES, LFP_TEXEL_F16, LFP_TEXEL_F32, LfpError)
+
+__all__ = ["lfp", "ProbeGrid", "make_views", "render", "LfpError", "LFP_TEXEL_F32", "LFP_TEXEL_F16",
+           "LFP_CLASS_MISS", "LFP_CLASS_HIT", "LFP_CLASS_UNKNOWN", "LFP_CLASS_STEPLIMIT",
+           "LFP_MARCH_HIER", "LFP_MARCH_FLAT", "LFP_SCHED_TILES", "LFP_SCHED_PERSISTENT"]
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_views(views) -> tuple:
+    """Pack camera views (objects with pos, right, up, fwd, fov_y, W, H) into a
+    ctypes lfp_view array with consecutive output offsets. Returns
+    (array, n_views, total_pixels)."""
+    arr = (lfp.lfp_view * len(views))()
+    off = 0
+    for k, v in enumerate(views):
+        a = arr[k]
+        for i in range(3):
+            a.pos[i], a.right[i], a.up[i], a.fwd[i] = v.pos[i], v.right[i], v.up[i], v.fwd[i]
+        a.fov_y, a.W, a.H, a.out_offset = v.fov_y, v.W, v.H, off
+        off += v.W * v.H
+    return arr, len(views), off
+
+
+class ProbeGrid:
+    """A probe grid on the current CUDA device (owns one lfp_grid handle).
+
+    spec: object with nx, ny, nz, origin, spacing, N, M (e.g. synth.Grid).
+    """
+
+    def __init__(self, spec, radiance_fmt=LFP_TEXEL_F32, normal_fmt=LFP_TEXEL_F32, thickness_rel=1.0,
+                 eye_eps=0.0, max_steps=0):
+        d = lfp.lfp_grid_desc()
+        d.nx, d.ny, d.nz = spec.nx, spec.ny, spec.nz
+        for i in range(3):
+            d.origin[i] = spec.origin[i]
+        d.spacing, d.N, d.M = spec.spacing, spec.N, spec.M
+        d.radiance_fmt, d.normal_fmt = radiance_fmt, normal_fmt
+        d.thickness_rel, d.eye_eps, d.max_steps = thickness_rel, eye_eps, max_steps
+        self.desc = d
+        self.spec = spec
+        self.N, self.M = spec.N, spec.M
+        self.n_probes = spec.nx * spec.ny * spec.nz
+        self.handle = lfp.lfp_create_grid(d)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lfp.lfp_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device_bytes(self) -> int:
+        return lfp.lfp_grid_bytes(self.desc)
+
+    def upload(self, dist, normal, radiance, first_probe=0, stream=None):
+        """Upload probe maps (numpy float32 host arrays or CUDA float32 tensors):
+        dist [P][N][N], normal [P][N][N][3], radiance [P][N][N][3]."""
+        import numpy as np
+        import torch
+        pl = lfp.lfp_probe_planes()
+        if isinstance(dist, torch.Tensor):
+            keep = [t.contiguous() for t in (dist, normal, radiance)]
+            for t in keep:
+                if t.dtype != torch.float32 or not t.is_cuda:
+                    raise ValueError("device probe planes must be CUDA float32 tensors")
+            pl.dist, pl.normal, pl.radiance = (t.data_ptr() for t in keep)
+            pl.is_device = 1
+        else:
+            keep = [np.ascontiguousarray(a, dtype=np.float32) for a in (dist, normal, radiance)]
+            pl.dist, pl.normal, pl.radiance = (a.ctypes.data for a in keep)
+            pl.is_device = 0
+        count = keep[0].shape[0]
+        s = _stream_handle(stream)
+        lfp.lfp_upload_probes(self.handle, first_probe, count, pl, s)
+        if not pl.is_device:  # host planes must outlive the asynchronous copies
+            torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def set_radiance(self, radiance, stream=None):
+        """Replace all probes' radiance from a CUDA float32 tensor [P][N][N][3]."""
+        r = radiance.contiguous()
+        lfp.lfp_set_radiance(self.handle, ctypes.c_void_p(r.data_ptr()), _stream_handle(stream))
+
+    def render(self, views, aux=True, hit_texel=False, counters=False, march=LFP_MARCH_HIER, tile=None,
+               schedule=0, stream=None):
+        """Render views; returns a dict of CUDA tensors: rgb [P,3] f32,
+        cls [P] u8, and optionally probe [P] i32, uv [P,2] f32, texel [P] i32,
+        counters [8] i64 (see lfp.COUNTER_NAMES)."""
+        import torch
+        arr, n, total = make_views(views)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = {"rgb": torch.empty((total, 3), dtype=torch.float32, device=dev),
+               "cls": torch.empty(total, dtype=torch.uint8, device=dev)}
+        if aux:
+            out["probe"] = torch.empty(total, dtype=torch.int32, device=dev)
+            out["uv"] = torch.empty((total, 2), dtype=torch.float32, device=dev)
+        if hit_texel:
+            out["texel"] = torch.empty(total, dtype=torch.int32, device=dev)
+        if counters:
+            out["counters"] = torch.zeros(lfp.N_COUNTERS, dtype=torch.int64, device=dev)
+        o = lfp.lfp_outputs()
+        o.rgb, o.cls = out["rgb"].data_ptr(), out["cls"].data_ptr()
+        o.aux_probe = out["probe"].data_ptr() if aux else None
+        o.aux_uv = out["uv"].data_ptr() if aux else None
+        o.hit_texel = out["texel"].data_ptr() if hit_texel else None
+        o.counters = out["counters"].data_ptr() if counters else None
+        opts = lfp.lfp_render_opts()
+        opts.march = march
+        if tile is not None:
+            opts.tile_w, opts.tile_h = tile
+        opts.schedule = schedule
+        lfp.lfp_render_ex(self.handle, arr, n, o, opts, _stream_handle(stream))
+        return out
+
+    def render_backward(self, views, grad_rgb, cls, probe, uv, grad_radiance=None, stream=None):
+        """Adjoint: accumulate into grad_radiance [P][N][N][3] f32 (zeros if None) and return it."""
+        import torch
+        arr, n, total = make_views(views)
+        if grad_radiance is None:
+            grad_radiance = torch.zeros((self.n_probes, self.N, self.N, 3), dtype=torch.float32,
+                                        device=grad_rgb.device)
+        g = grad_rgb.contiguous()
+        lfp.lfp_render_backward(self.handle, arr, n, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(cls.data_ptr()),
+                                ctypes.c_void_p(probe.data_ptr()), ctypes.c_void_p(uv.data_ptr()),
+                                ctypes.c_void_p(grad_radiance.data_ptr()), _stream_handle(stream))
+        return grad_radiance
+
+    def render_to_host(self, views, rgb_host, cls_host, stream=None):
+        """One C-ABI call: render into grid-owned device buffers and copy rgb
+        and cls into the given host tensors (pinned for asynchronous copies)."""
+        arr, n, total = make_views(views)
+        lfp.lfp_render_to_host(self.handle, arr, n, ctypes.c_void_p(rgb_host.data_ptr()),
+                               ctypes.c_void_p(cls_host.data_ptr()), _stream_handle(stream))
+
+    def check_flags(self, stream=None) -> int:
+        return lfp.lfp_check_flags(self.handle, _stream_handle(stream))
+
+
+def _autograd():
+    import torch
+
+    class LfpRender(torch.autograd.Function):
+        """rgb = render(radiance): forward through the tracer, backward through
+        the adjoint kernel (rgb is linear in radiance for fixed geometry)."""
+
+        @staticmethod
+        def forward(ctx, radiance, grid: ProbeGrid, views):
+            grid.set_radiance(radiance.detach())
+            out = grid.render(views, aux=True)
+            ctx.grid, ctx.views = grid, views
+            ctx.save_for_backward(out["cls"], out["probe"], out["uv"])
+            ctx.mark_non_differentiable(out["cls"])
+            return out["rgb"], out["cls"]
+
+        @staticmethod
+        def backward(ctx, grad_rgb, grad_cls):
+            cls, probe, uv = ctx.saved_tensors
+            g = ctx.grid.render_backward(ctx.views, grad_rgb, cls, probe, uv)
+            return g, None, None
+
+    return LfpRender
+
+
+_LfpRender = None
+
+
+def render(radiance, grid: ProbeGrid, views):
+    """Differentiable render: radiance [P][N][N][3] f32 CUDA tensor -> (rgb [pixels,3], cls [pixels])."""
+    global _LfpRender
+    if _LfpRender is None:
+        _LfpRender = _autograd()
+    return _LfpRender.apply(radiance, grid, views)

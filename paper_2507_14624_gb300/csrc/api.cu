@@ -1,0 +1,434 @@
+// Host side of the C ABI declared in include/lfp.h: argument checks, device
+// storage owned by the grid, upload + min/max map build, batching of views
+// into launches, the adjoint and the host-buffer render.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lfp.h"
+#include "lfp_internal.h"
+
+using namespace lfp;
+
+struct lfp_grid {
+    lfp_grid_desc desc;
+    int P = 0;
+    int device = 0;
+    int sm_count = 0;
+    float* dist = nullptr;
+    float2* mip = nullptr;
+    void* nrm = nullptr;
+    void* rad = nullptr;
+    unsigned* flags = nullptr;          // device flag word
+    unsigned* tile_counter = nullptr;   // persistent-schedule work queue head
+    float* staging = nullptr;
+    size_t staging_bytes = 0;
+    float* host_rgb = nullptr;          // device buffers behind lfp_render_to_host
+    uint8_t* host_cls = nullptr;
+    long long host_pixels = 0;
+    std::vector<unsigned char> uploaded;
+    int tile_w = 16, tile_h = 8;        // default ray tile
+    int schedule = LFP_SCHED_TILES;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+std::atomic<long long> g_alloc_count{0};
+
+// Device allocation with host-side fault injection: LFP_FAULT_ALLOC_FAIL=n
+// makes the n-th allocation of the process fail with LFP_ERR_OOM before any
+// CUDA call, so error paths can be tested without a GPU.
+lfp_status dev_alloc(void** p, size_t bytes) {
+    long long n = ++g_alloc_count;
+    if (const char* f = std::getenv("LFP_FAULT_ALLOC_FAIL")) {
+        long long k = std::atoll(f);
+        if (k > 0 && n == k) return LFP_ERR_OOM;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return LFP_ERR_OOM;
+    }
+    return e == cudaSuccess ? LFP_OK : LFP_ERR_CUDA;
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+#define LFP_CUDA(call)                                   \
+    do {                                                 \
+        if ((call) != cudaSuccess) return LFP_ERR_CUDA;  \
+    } while (0)
+#define LFP_TRY(call)                      \
+    do {                                   \
+        lfp_status st_ = (call);           \
+        if (st_ != LFP_OK) return st_;     \
+    } while (0)
+
+// Makes the grid's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+size_t nrm_bytes(int fmt) { return fmt == LFP_TEXEL_F32 ? 8 : 4; }
+size_t rad_bytes(int fmt) { return fmt == LFP_TEXEL_F32 ? 16 : 8; }
+
+lfp_status check_desc(const lfp_grid_desc* d) {
+    if (!d) return LFP_ERR_INVALID_ARG;
+    if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 4096 || d->ny > 4096 || d->nz > 4096) return LFP_ERR_INVALID_ARG;
+    if ((long long)d->nx * d->ny * d->nz > (1LL << 24)) return LFP_ERR_INVALID_ARG;
+    if (!(d->spacing > 0.0f) || !std::isfinite(d->spacing) || !finite3(d->origin)) return LFP_ERR_INVALID_ARG;
+    if (d->N < 2 || d->N > 8192 || (d->N & 1)) return LFP_ERR_INVALID_ARG;
+    if (d->M < 2 || d->M > d->N || (d->M & 1) || d->N % d->M) return LFP_ERR_INVALID_ARG;
+    if ((d->radiance_fmt != LFP_TEXEL_F32 && d->radiance_fmt != LFP_TEXEL_F16) ||
+        (d->normal_fmt != LFP_TEXEL_F32 && d->normal_fmt != LFP_TEXEL_F16))
+        return LFP_ERR_INVALID_ARG;
+    if (!std::isfinite(d->thickness_rel) || !std::isfinite(d->eye_eps) || d->eye_eps < 0.0f || d->max_steps < 0)
+        return LFP_ERR_INVALID_ARG;
+    return LFP_OK;
+}
+
+lfp_status check_views(const lfp_view* views, int n_views) {
+    if (!views || n_views < 1) return LFP_ERR_INVALID_ARG;
+    for (int i = 0; i < n_views; ++i) {
+        const lfp_view& v = views[i];
+        if (v.W < 1 || v.H < 1 || (long long)v.W * v.H > (1LL << 31) || v.out_offset < 0) return LFP_ERR_INVALID_ARG;
+        if (!finite3(v.pos) || !finite3(v.right) || !finite3(v.up) || !finite3(v.fwd)) return LFP_ERR_INVALID_ARG;
+        if (!(v.fov_y > 0.0f) || !(v.fov_y < 3.1415926f)) return LFP_ERR_INVALID_ARG;
+    }
+    return LFP_OK;
+}
+
+GridDev grid_dev(const lfp_grid* g) {
+    GridDev d;
+    const lfp_grid_desc& s = g->desc;
+    d.nx = s.nx;
+    d.ny = s.ny;
+    d.nz = s.nz;
+    d.ox = s.origin[0];
+    d.oy = s.origin[1];
+    d.oz = s.origin[2];
+    d.spacing = s.spacing;
+    d.N = s.N;
+    d.M = s.M;
+    d.k = s.N / s.M;
+    d.two_way = s.thickness_rel < 0.0f ? 1 : 0;
+    d.kappa = (float)(1.0 + 4.0 * (double)std::max(s.thickness_rel, 0.0f) / s.N);
+    d.eye_eps = s.eye_eps > 0.0f ? s.eye_eps : 1e-6f * s.spacing;
+    d.max_steps = s.max_steps;
+    d.dist = g->dist;
+    d.mip = g->mip;
+    d.nrm = g->nrm;
+    d.rad = g->rad;
+    d.flags = g->flags;
+    return d;
+}
+
+ViewDev view_dev(const lfp_view& v, int tw, int th, int tile_begin) {
+    ViewDev d;
+    d.px = v.pos[0]; d.py = v.pos[1]; d.pz = v.pos[2];
+    d.rx = v.right[0]; d.ry = v.right[1]; d.rz = v.right[2];
+    d.ux = v.up[0]; d.uy = v.up[1]; d.uz = v.up[2];
+    d.fx = v.fwd[0]; d.fy = v.fwd[1]; d.fz = v.fwd[2];
+    double t = std::tan(0.5 * (double)v.fov_y);
+    d.sa = (float)(t * v.W / v.H);
+    d.sb = (float)t;
+    d.W = v.W;
+    d.H = v.H;
+    d.out_offset = v.out_offset;
+    d.tiles_x = (v.W + tw - 1) / tw;
+    d.tile_begin = tile_begin;
+    return d;
+}
+
+bool valid_tile(int w, int h) {
+    return (w == 8 && h == 4) || (w == 8 && h == 8) || (w == 16 && h == 8) || (w == 16 && h == 16) ||
+           (w == 32 && h == 8);
+}
+
+lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const OutDev& out,
+                       const lfp_render_opts* opts, cudaStream_t s) {
+    int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0;
+    if (opts) {
+        if (opts->tile_w || opts->tile_h) {
+            if (!valid_tile(opts->tile_w, opts->tile_h)) return LFP_ERR_INVALID_ARG;
+            tw = opts->tile_w;
+            th = opts->tile_h;
+        }
+        if (opts->march != LFP_MARCH_HIER && opts->march != LFP_MARCH_FLAT) return LFP_ERR_INVALID_ARG;
+        flat = opts->march == LFP_MARCH_FLAT;
+        if (opts->schedule < LFP_SCHED_AUTO || opts->schedule > LFP_SCHED_PERSISTENT) return LFP_ERR_INVALID_ARG;
+        if (opts->schedule != LFP_SCHED_AUTO) sched = opts->schedule;
+    }
+    for (unsigned char u : g->uploaded)
+        if (!u) return LFP_ERR_STATE;
+    GridDev gd = grid_dev(g);
+    RenderLaunch L;
+    L.flat = flat;
+    L.persistent = sched == LFP_SCHED_PERSISTENT;
+    L.tile_counter = g->tile_counter;
+    L.persistent_blocks = 0;
+    if (L.persistent) {
+        int per_sm = render_max_active_blocks(g->desc.radiance_fmt, g->desc.normal_fmt, tw * th);
+        L.persistent_blocks = std::max(1, per_sm) * g->sm_count;
+    }
+    static thread_local ViewBatch vb;  // ~10 KB: keep it off the host stack
+    for (int first = 0; first < n_views; first += kMaxViewsPerLaunch) {
+        int n = std::min(kMaxViewsPerLaunch, n_views - first);
+        vb.n = n;
+        vb.tile_w = tw;
+        vb.tile_h = th;
+        long long tiles = 0;
+        for (int i = 0; i < n; ++i) {
+            const lfp_view& v = views[first + i];
+            vb.v[i] = view_dev(v, tw, th, (int)tiles);
+            tiles += (long long)vb.v[i].tiles_x * ((v.H + th - 1) / th);
+            if (tiles > (1LL << 31) - 1) return LFP_ERR_INVALID_ARG;
+        }
+        vb.total_tiles = (int)tiles;
+        if (L.persistent) LFP_CUDA(cudaMemsetAsync(g->tile_counter, 0, sizeof(unsigned), s));
+        LFP_CUDA(launch_render(gd, g->desc.radiance_fmt, g->desc.normal_fmt, vb, out, L, s));
+    }
+    return LFP_OK;
+}
+
+void destroy(lfp_grid* g) {
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    cudaDeviceSynchronize();
+    dev_free(g->dist);
+    dev_free(g->mip);
+    dev_free(g->nrm);
+    dev_free(g->rad);
+    dev_free(g->flags);
+    dev_free(g->tile_counter);
+    dev_free(g->staging);
+    dev_free(g->host_rgb);
+    dev_free(g->host_cls);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lfp_status_string(lfp_status s) {
+    switch (s) {
+        case LFP_OK: return "ok";
+        case LFP_ERR_INVALID_ARG: return "invalid argument";
+        case LFP_ERR_OOM: return "out of device memory";
+        case LFP_ERR_CUDA: return "CUDA error";
+        case LFP_ERR_STATE: return "invalid call order (e.g. probes not uploaded)";
+        case LFP_WARN_STEPLIMIT: return "some rays reached the step limit";
+    }
+    return "unknown status";
+}
+
+lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes) {
+    LFP_TRY(check_desc(desc));
+    if (!bytes) return LFP_ERR_INVALID_ARG;
+    unsigned long long P = (unsigned long long)desc->nx * desc->ny * desc->nz;
+    unsigned long long NN = (unsigned long long)desc->N * desc->N, MM = (unsigned long long)desc->M * desc->M;
+    *bytes = P * (NN * (4 + nrm_bytes(desc->normal_fmt) + rad_bytes(desc->radiance_fmt)) + MM * 8);
+    return LFP_OK;
+}
+
+lfp_status lfp_create_grid(const lfp_grid_desc* desc, lfp_grid** out) {
+    if (!out) return LFP_ERR_INVALID_ARG;
+    *out = nullptr;
+    LFP_TRY(check_desc(desc));
+    lfp_grid* g = new (std::nothrow) lfp_grid();
+    if (!g) return LFP_ERR_OOM;
+    g->desc = *desc;
+    g->P = desc->nx * desc->ny * desc->nz;
+    g->uploaded.assign(g->P, 0);
+    size_t NN = (size_t)desc->N * desc->N, MM = (size_t)desc->M * desc->M;
+    lfp_status st = LFP_OK;
+    if (st == LFP_OK) st = dev_alloc((void**)&g->dist, g->P * NN * 4);
+    if (st == LFP_OK) st = dev_alloc((void**)&g->mip, g->P * MM * 8);
+    if (st == LFP_OK) st = dev_alloc(&g->nrm, g->P * NN * nrm_bytes(desc->normal_fmt));
+    if (st == LFP_OK) st = dev_alloc(&g->rad, g->P * NN * rad_bytes(desc->radiance_fmt));
+    if (st == LFP_OK) st = dev_alloc((void**)&g->flags, 2 * sizeof(unsigned));
+    if (st == LFP_OK) st = dev_alloc((void**)&g->tile_counter, sizeof(unsigned));
+    if (st == LFP_OK && (cudaGetDevice(&g->device) != cudaSuccess ||
+                         cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess ||
+                         cudaMemset(g->flags, 0, 2 * sizeof(unsigned)) != cudaSuccess))
+        st = LFP_ERR_CUDA;
+    if (st != LFP_OK) {
+        destroy(g);
+        return st;
+    }
+    *out = g;
+    return LFP_OK;
+}
+
+void lfp_destroy_grid(lfp_grid* g) { destroy(g); }
+
+lfp_status lfp_upload_probes(lfp_grid* g, int first_probe, int count, const lfp_probe_planes* pl, void* stream) {
+    if (!g || !pl || !pl->dist || !pl->normal || !pl->radiance) return LFP_ERR_INVALID_ARG;
+    if (first_probe < 0 || count < 1 || (long long)first_probe + count > g->P) return LFP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = g->desc.N;
+    size_t NN = (size_t)N * N;
+    float* dist_dst = g->dist + (size_t)first_probe * NN;
+    char* nrm_dst = (char*)g->nrm + (size_t)first_probe * NN * nrm_bytes(g->desc.normal_fmt);
+    char* rad_dst = (char*)g->rad + (size_t)first_probe * NN * rad_bytes(g->desc.radiance_fmt);
+    if (pl->is_device) {
+        LFP_CUDA(cudaMemcpyAsync(dist_dst, pl->dist, count * NN * 4, cudaMemcpyDeviceToDevice, s));
+        LFP_CUDA(launch_encode_normals(pl->normal, nrm_dst, g->desc.normal_fmt, (long long)count * NN, s));
+        LFP_CUDA(launch_convert_radiance(pl->radiance, rad_dst, g->desc.radiance_fmt, (long long)count * NN, s));
+    } else {
+        LFP_CUDA(cudaMemcpyAsync(dist_dst, pl->dist, count * NN * 4, cudaMemcpyHostToDevice, s));
+        // xyz / rgb planes go through a grid-owned staging buffer, a few probes at a time
+        size_t per_probe = NN * 3 * sizeof(float);
+        int chunk = (int)std::max<size_t>(1, std::min<size_t>(count, (64u << 20) / per_probe));
+        if (g->staging_bytes < chunk * per_probe) {
+            LFP_CUDA(cudaStreamSynchronize(s));
+            dev_free(g->staging);
+            g->staging = nullptr;
+            g->staging_bytes = 0;
+            LFP_TRY(dev_alloc((void**)&g->staging, chunk * per_probe));
+            g->staging_bytes = chunk * per_probe;
+        }
+        for (int c0 = 0; c0 < count; c0 += chunk) {
+            int c = std::min(chunk, count - c0);
+            long long n = (long long)c * NN;
+            LFP_CUDA(cudaMemcpyAsync(g->staging, pl->normal + (size_t)c0 * NN * 3, n * 12, cudaMemcpyHostToDevice, s));
+            LFP_CUDA(launch_encode_normals(g->staging, nrm_dst + (size_t)c0 * NN * nrm_bytes(g->desc.normal_fmt),
+                                           g->desc.normal_fmt, n, s));
+            LFP_CUDA(cudaMemcpyAsync(g->staging, pl->radiance + (size_t)c0 * NN * 3, n * 12, cudaMemcpyHostToDevice, s));
+            LFP_CUDA(launch_convert_radiance(g->staging, rad_dst + (size_t)c0 * NN * rad_bytes(g->desc.radiance_fmt),
+                                             g->desc.radiance_fmt, n, s));
+        }
+    }
+    LFP_CUDA(launch_build_mip(dist_dst, g->mip + (size_t)first_probe * g->desc.M * g->desc.M, count, N, g->desc.M, s));
+    for (int p = first_probe; p < first_probe + count; ++p) g->uploaded[p] = 1;
+    return LFP_OK;
+}
+
+lfp_status lfp_render_ex(lfp_grid* g, const lfp_view* views, int n_views, const lfp_outputs* o,
+                         const lfp_render_opts* opts, void* stream) {
+    if (!g || !o) return LFP_ERR_INVALID_ARG;
+    LFP_TRY(check_views(views, n_views));
+    if (o->aux_uv && ((uintptr_t)o->aux_uv & 3)) return LFP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    OutDev out;
+    out.rgb = o->rgb;
+    out.cls = o->cls;
+    out.aux_probe = o->aux_probe;
+    out.aux_uv = o->aux_uv;
+    out.hit_texel = o->hit_texel;
+    out.counters = o->counters;
+    return render_impl(g, views, n_views, out, opts, (cudaStream_t)stream);
+}
+
+lfp_status lfp_render(lfp_grid* g, const lfp_view* views, int n_views, float* rgb, uint8_t* cls,
+                      int32_t* aux_probe, float* aux_uv, void* stream) {
+    if (!rgb || !cls) return LFP_ERR_INVALID_ARG;
+    lfp_outputs o;
+    std::memset(&o, 0, sizeof(o));
+    o.rgb = rgb;
+    o.cls = cls;
+    o.aux_probe = aux_probe;
+    o.aux_uv = aux_uv;
+    return lfp_render_ex(g, views, n_views, &o, nullptr, stream);
+}
+
+lfp_status lfp_render_to_host(lfp_grid* g, const lfp_view* views, int n_views, float* rgb_host, uint8_t* cls_host,
+                              void* stream) {
+    if (!g) return LFP_ERR_INVALID_ARG;
+    LFP_TRY(check_views(views, n_views));
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    long long total = 0;
+    for (int i = 0; i < n_views; ++i)
+        total = std::max(total, views[i].out_offset + (long long)views[i].W * views[i].H);
+    if (total > g->host_pixels) {
+        LFP_CUDA(cudaStreamSynchronize(s));
+        dev_free(g->host_rgb);
+        dev_free(g->host_cls);
+        g->host_rgb = nullptr;
+        g->host_cls = nullptr;
+        g->host_pixels = 0;
+        LFP_TRY(dev_alloc((void**)&g->host_rgb, total * 12));
+        LFP_TRY(dev_alloc((void**)&g->host_cls, total));
+        g->host_pixels = total;
+    }
+    OutDev out;
+    std::memset(&out, 0, sizeof(out));
+    out.rgb = g->host_rgb;
+    out.cls = g->host_cls;
+    LFP_TRY(render_impl(g, views, n_views, out, nullptr, s));
+    if (rgb_host) LFP_CUDA(cudaMemcpyAsync(rgb_host, g->host_rgb, total * 12, cudaMemcpyDeviceToHost, s));
+    if (cls_host) LFP_CUDA(cudaMemcpyAsync(cls_host, g->host_cls, total, cudaMemcpyDeviceToHost, s));
+    LFP_CUDA(cudaStreamSynchronize(s));
+    return LFP_OK;
+}
+
+lfp_status lfp_render_backward(lfp_grid* g, const lfp_view* views, int n_views, const float* grad_rgb,
+                               const uint8_t* cls, const int32_t* aux_probe, const float* aux_uv,
+                               float* grad_radiance, void* stream) {
+    if (!g || !grad_rgb || !cls || !aux_probe || !aux_uv || !grad_radiance) return LFP_ERR_INVALID_ARG;
+    LFP_TRY(check_views(views, n_views));
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    static thread_local PixBatch pb;
+    for (int first = 0; first < n_views; first += kMaxViewsPerLaunch) {
+        int n = std::min(kMaxViewsPerLaunch, n_views - first);
+        pb.n = n;
+        pb.begin[0] = 0;
+        for (int i = 0; i < n; ++i) {
+            const lfp_view& v = views[first + i];
+            pb.out_offset[i] = v.out_offset;
+            pb.begin[i + 1] = pb.begin[i] + (long long)v.W * v.H;
+        }
+        LFP_CUDA(launch_backward(g->desc.N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, (cudaStream_t)stream));
+    }
+    return LFP_OK;
+}
+
+lfp_status lfp_set_radiance(lfp_grid* g, const float* dev_rad, void* stream) {
+    if (!g || !dev_rad) return LFP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    long long n = (long long)g->P * g->desc.N * g->desc.N;
+    LFP_CUDA(launch_convert_radiance(dev_rad, g->rad, g->desc.radiance_fmt, n, (cudaStream_t)stream));
+    return LFP_OK;
+}
+
+lfp_status lfp_check_flags(lfp_grid* g, void* stream) {
+    if (!g) return LFP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned flags = 0;
+    LFP_CUDA(cudaMemcpyAsync(&flags, g->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    LFP_CUDA(cudaStreamSynchronize(s));
+    LFP_CUDA(cudaMemsetAsync(g->flags, 0, sizeof(unsigned), s));
+    return (flags & 1u) ? LFP_WARN_STEPLIMIT : LFP_OK;
+}
+
+}  // extern "C"

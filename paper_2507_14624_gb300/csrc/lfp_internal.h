@@ -1,0 +1,29 @@
+// Internal interface between the C-ABI host code and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lfp_device.cuh"
+
+namespace lfp {
+
+struct RenderLaunch {
+    int flat;                 // full-resolution march only (Appendix A RayMarching)
+    int persistent;           // persistent CTAs pulling tiles from tile_counter
+    int persistent_blocks;
+    unsigned* tile_counter;   // zeroed by the caller before a persistent launch
+};
+
+cudaError_t launch_render(const GridDev& g, int rad_fmt, int nrm_fmt, const ViewBatch& vb, const OutDev& out,
+                          const RenderLaunch& L, cudaStream_t s);
+int render_max_active_blocks(int rad_fmt, int nrm_fmt, int threads);
+
+// upload-time conversions: xyz normals -> octahedral RG, RGB -> RGBA texels
+cudaError_t launch_encode_normals(const float* xyz, void* nrm, int nrm_fmt, long long n, cudaStream_t s);
+cudaError_t launch_convert_radiance(const float* rgb, void* rad, int rad_fmt, long long n, cudaStream_t s);
+// per-block min/max of the distance maps for `count` probes
+cudaError_t launch_build_mip(const float* dist, float2* mip, int count, int N, int M, cudaStream_t s);
+// adjoint scatter into grad_radiance [P][N][N][3]
+cudaError_t launch_backward(int N, const PixBatch& pb, const float* grad_rgb, const uint8_t* cls,
+                            const int32_t* aux_probe, const float* aux_uv, float* grad_rad, cudaStream_t s);
+
+}  // namespace lfp

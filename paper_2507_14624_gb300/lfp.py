@@ -1,0 +1,149 @@
+"""ctypes binding of the C ABI in include/lfp.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; every step of
+the tracer runs in the CUDA library. PyTorch supplies device memory (tensor
+data pointers) and streams. The library is loaded from the package directory;
+if it is missing the import fails -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblfp.so")
+
+# status codes
+LFP_OK, LFP_ERR_INVALID_ARG, LFP_ERR_OOM, LFP_ERR_CUDA, LFP_ERR_STATE = 0, 1, 2, 3, 4
+LFP_WARN_STEPLIMIT = 100
+LFP_TEXEL_F32, LFP_TEXEL_F16 = 0, 1
+LFP_CLASS_MISS, LFP_CLASS_HIT, LFP_CLASS_UNKNOWN, LFP_CLASS_STEPLIMIT = 0, 1, 2, 3
+LFP_MARCH_HIER, LFP_MARCH_FLAT = 0, 1
+LFP_SCHED_AUTO, LFP_SCHED_TILES, LFP_SCHED_PERSISTENT = 0, 1, 2
+N_COUNTERS = 8
+COUNTER_NAMES = ("coarse", "fine", "normal", "radiance", "cells", "probes", "hits", "rays")
+
+
+class lfp_grid_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("origin", ctypes.c_float * 3), ("spacing", ctypes.c_float),
+                ("N", ctypes.c_int), ("M", ctypes.c_int),
+                ("radiance_fmt", ctypes.c_int), ("normal_fmt", ctypes.c_int),
+                ("thickness_rel", ctypes.c_float), ("eye_eps", ctypes.c_float),
+                ("max_steps", ctypes.c_int)]
+
+
+class lfp_view(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_float * 3), ("right", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("fwd", ctypes.c_float * 3), ("fov_y", ctypes.c_float), ("W", ctypes.c_int),
+                ("H", ctypes.c_int), ("out_offset", ctypes.c_longlong)]
+
+
+class lfp_probe_planes(ctypes.Structure):
+    _fields_ = [("dist", ctypes.c_void_p), ("normal", ctypes.c_void_p), ("radiance", ctypes.c_void_p),
+                ("is_device", ctypes.c_int)]
+
+
+class lfp_outputs(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("cls", ctypes.c_void_p), ("aux_probe", ctypes.c_void_p),
+                ("aux_uv", ctypes.c_void_p), ("hit_texel", ctypes.c_void_p), ("counters", ctypes.c_void_p)]
+
+
+class lfp_render_opts(ctypes.Structure):
+    _fields_ = [("march", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
+                ("schedule", ctypes.c_int)]
+
+
+class LfpError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {lfp_status_string(status)} ({status})")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is missing: run paper_2507_14624_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, P = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER
+    sig = {
+        "lfp_create_grid": ([P(lfp_grid_desc), P(vp)], i),
+        "lfp_upload_probes": ([vp, i, i, P(lfp_probe_planes), vp], i),
+        "lfp_render": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp], i),
+        "lfp_render_ex": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
+        "lfp_render_to_host": ([vp, P(lfp_view), i, vp, vp, vp], i),
+        "lfp_render_backward": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, vp], i),
+        "lfp_set_radiance": ([vp, vp, vp], i),
+        "lfp_check_flags": ([vp, vp], i),
+        "lfp_grid_bytes": ([P(lfp_grid_desc), P(ctypes.c_ulonglong)], i),
+        "lfp_destroy_grid": ([vp], None),
+        "lfp_status_string": ([i], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int, what: str) -> int:
+    if status not in (LFP_OK, LFP_WARN_STEPLIMIT):
+        raise LfpError(status, what)
+    return status
+
+
+def lfp_status_string(status: int) -> str:
+    return _lib.lfp_status_string(status).decode()
+
+
+def lfp_create_grid(desc: lfp_grid_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.lfp_create_grid(ctypes.byref(desc), ctypes.byref(h)), "lfp_create_grid")
+    return h.value
+
+
+def lfp_destroy_grid(grid) -> None:
+    _lib.lfp_destroy_grid(grid)
+
+
+def lfp_upload_probes(grid, first_probe: int, count: int, planes: lfp_probe_planes, stream) -> None:
+    _check(_lib.lfp_upload_probes(grid, first_probe, count, ctypes.byref(planes), stream), "lfp_upload_probes")
+
+
+def lfp_render(grid, views, n_views, rgb, cls, aux_probe, aux_uv, stream) -> None:
+    _check(_lib.lfp_render(grid, views, n_views, rgb, cls, aux_probe, aux_uv, stream), "lfp_render")
+
+
+def lfp_render_ex(grid, views, n_views, outputs: lfp_outputs, opts: lfp_render_opts | None, stream) -> None:
+    _check(_lib.lfp_render_ex(grid, views, n_views, ctypes.byref(outputs),
+                              ctypes.byref(opts) if opts is not None else None, stream), "lfp_render_ex")
+
+
+def lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream) -> None:
+    _check(_lib.lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream), "lfp_render_to_host")
+
+
+def lfp_render_backward(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, stream) -> None:
+    _check(_lib.lfp_render_backward(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, stream),
+           "lfp_render_backward")
+
+
+def lfp_set_radiance(grid, dev_radiance, stream) -> None:
+    _check(_lib.lfp_set_radiance(grid, dev_radiance, stream), "lfp_set_radiance")
+
+
+def lfp_check_flags(grid, stream) -> int:
+    return _check(_lib.lfp_check_flags(grid, stream), "lfp_check_flags")
+
+
+def lfp_grid_bytes(desc: lfp_grid_desc) -> int:
+    b = ctypes.c_ulonglong()
+    _check(_lib.lfp_grid_bytes(ctypes.byref(desc), ctypes.byref(b)), "lfp_grid_bytes")
+    return b.value
+
+
+def raw_call(name: str, *args) -> int:
+    """Call an entry point and return its raw status (for argument-validation tests)."""
+    return getattr(_lib, name)(*args)

@@ -1,0 +1,105 @@
+"""Host-side checks of the C ABI (no GPU needed): exports, argument
+validation, status strings, byte accounting and allocation fault injection."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lfp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_14624_gb300 import build
+    build.build()
+    from paper_2507_14624_gb300 import lfp
+    return lfp
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lfp_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    names = declared_functions()
+    assert {"lfp_create_grid", "lfp_upload_probes", "lfp_render", "lfp_render_backward"} <= set(names)
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (lfp_\w+)", out))
+    assert set(names) <= exported
+
+
+def _desc(lfp, **kw):
+    d = lfp.lfp_grid_desc()
+    d.nx = d.ny = d.nz = 2
+    d.spacing, d.N, d.M = 1.0, 64, 16
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("field,value", [("nx", 1), ("N", 63), ("M", 3), ("M", 128), ("N", 48 * 0 + 100),
+                                         ("spacing", 0.0), ("spacing", float("nan")), ("radiance_fmt", 7),
+                                         ("max_steps", -1), ("eye_eps", -1.0)])
+def test_invalid_descriptors_are_rejected(lib, field, value):
+    d = _desc(lib, **{field: value})
+    if field == "N" and value == 100:
+        d.M = 16  # 100 % 16 != 0
+    h = ctypes.c_void_p(123)
+    st = lib.raw_call("lfp_create_grid", ctypes.byref(d), ctypes.byref(h))
+    assert st == lib.LFP_ERR_INVALID_ARG
+    assert h.value is None  # *out is cleared on failure
+    b = ctypes.c_ulonglong()
+    assert lib.raw_call("lfp_grid_bytes", ctypes.byref(d), ctypes.byref(b)) == lib.LFP_ERR_INVALID_ARG
+
+
+def test_null_arguments_are_rejected(lib):
+    L = lib
+    assert L.raw_call("lfp_create_grid", None, None) == L.LFP_ERR_INVALID_ARG
+    assert L.raw_call("lfp_upload_probes", None, 0, 1, None, None) == L.LFP_ERR_INVALID_ARG
+    assert L.raw_call("lfp_render", None, None, 1, None, None, None, None, None) == L.LFP_ERR_INVALID_ARG
+    assert L.raw_call("lfp_render_backward", None, None, 1, None, None, None, None, None, None) == L.LFP_ERR_INVALID_ARG
+    assert L.raw_call("lfp_set_radiance", None, None, None) == L.LFP_ERR_INVALID_ARG
+    assert L.raw_call("lfp_check_flags", None, None) == L.LFP_ERR_INVALID_ARG
+    L.lfp_destroy_grid(None)  # NULL-safe
+
+
+def test_status_strings(lib):
+    for s in (0, 1, 2, 3, 4, 100):
+        assert len(lib.lfp_status_string(s)) >= 2
+    assert lib.lfp_status_string(999) == "unknown status"
+
+
+def test_grid_bytes_accounting(lib):
+    """Storage per probe: N^2 (4 distance + normal + radiance) + M^2 * 8 bytes;
+    FP16 texels halve the normal (8 -> 4) and radiance (16 -> 8) bytes."""
+    d = _desc(lib, nx=4, ny=4, nz=4, N=256, M=16)
+    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 8 + 16) + 16 * 16 * 8)
+    d.radiance_fmt = d.normal_fmt = lib.LFP_TEXEL_F16
+    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 4 + 8) + 16 * 16 * 8)
+
+
+def test_allocation_fault_injection_returns_oom_without_a_device(lib):
+    """LFP_FAULT_ALLOC_FAIL=1 fails the first device allocation inside
+    lfp_create_grid before any CUDA call: the status is OOM and the handle
+    stays NULL (run in a fresh process so the allocation counter starts at 0)."""
+    code = (
+        "import ctypes, sys; sys.path.insert(0, %r)\n"
+        "from paper_2507_14624_gb300 import lfp\n"
+        "d = lfp.lfp_grid_desc(); d.nx = d.ny = d.nz = 2; d.spacing = 1.0; d.N = 64; d.M = 16\n"
+        "h = ctypes.c_void_p(7)\n"
+        "st = lfp.raw_call('lfp_create_grid', ctypes.byref(d), ctypes.byref(h))\n"
+        "print(st, h.value)\n" % ROOT)
+    env = dict(os.environ, LFP_FAULT_ALLOC_FAIL="1", CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
+    assert out.returncode == 0, out.stderr
+    st, h = out.stdout.split()
+    assert int(st) == 2 and h == "None"
