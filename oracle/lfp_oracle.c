@@ -38,9 +38,14 @@
  *      "the ray can shoot from below the surface ... UNKNOWN" is read as the
  *      passes-behind branch. th < 0 selects the listing's two-way rule.
  *      Coarse texel: candidate iff r_hi >= dmin.
- *   R4 hit point: smallest root of r(t) = d in [ta, tb], else ta; shading
- *      direction = (X + t w - O) / r; radiance bilinear over texel centres
- *      with the octahedral mirror border.
+ *   R4 hit point (the listing returns the texel only): the first t >= ta at
+ *      which the ray reaches the stored distance, r(t) = d, clamped to
+ *      [ta, tb]; if the ray is behind the surface at ta and never comes back
+ *      to d, the point of closest approach (clamped), or ta when it recedes.
+ *      This is continuous in the data, unlike "a root inside [ta, tb], else
+ *      ta", which jumps by a texel when a root sits at an interval end.
+ *      Shading direction = (X + t w - O) / r; radiance bilinear over texel
+ *      centres with the octahedral mirror border.
  *   R5 grid iterator: 3D DDA over cells (Amanatides & Woo 1987). The first
  *      visited cell starts at t = 0, the last one (where the ray leaves the
  *      grid) ends at t = infinity. Cage order: distance from the corner
@@ -423,17 +428,18 @@ static int trace_one_ray_segment(trace_ctx* cx) {
     return cx->result;
 }
 
-/* Hit point (R4): smallest root of |Y0 + t w| = d in [ta, tb], else ta. */
+static double clampd(double t, double lo, double hi) { return t < lo ? lo : (t > hi ? hi : t); }
+
+/* Hit point (R4): |Y0 + t w|^2 = d^2 is A t^2 + 2 B t + C = 0. */
 static double hit_time(const oseg* sg, double ta, double tb, double d) {
     double A = dot3(sg->w, sg->w), B = dot3(sg->Y0, sg->w), C = dot3(sg->Y0, sg->Y0) - d * d;
     double disc = B * B - A * C;
-    if (disc >= 0.0) {
-        double sq = sqrt(disc);
-        double r1 = (-B - sq) / A, r2 = (-B + sq) / A;
-        if (r1 >= ta && r1 <= tb) return r1;
-        if (r2 >= ta && r2 <= tb) return r2;
-    }
-    return ta;
+    if (seg_radius(sg, ta) < d) /* in front at ta: the ray enters the surface at the larger root */
+        return clampd((-B + sqrt(disc > 0.0 ? disc : 0.0)) / A, ta, tb);
+    double tstar = -B / A;          /* closest approach to the probe */
+    if (tstar <= ta) return ta;     /* behind and receding */
+    if (disc < 0.0) return clampd(tstar, ta, tb);
+    return clampd((-B - sqrt(disc)) / A, ta, tb); /* approaching: the smaller root */
 }
 
 /* Octant split (Sec. 4.2: "at most 4 ray segments"): cut [t0, t1] where the

@@ -275,26 +275,27 @@ __device__ void trace_probe(const GridDev& g, const Ray& r, int probe, float t0,
     out.cls = kMiss;
 }
 
-// Hit point: smallest root of |Y0 + t w| = d in [ta, tb], else ta (roots
-// within rounding of the interval are clamped into it).
+// Hit point: the first t >= ta with |Y0 + t w| = d, clamped to [ta, tb];
+// when the ray is behind the stored surface at ta it is the smaller root if
+// the ray comes back to d, else the closest approach (ta when receding).
+// |Y0 + t w|^2 = d^2 is A t^2 + 2 B t + C = 0; the roots use the
+// cancellation-free forms.
 __device__ __forceinline__ float hit_time(const Seg& s, float ta, float tb, float d) {
     float A = s.w.x * s.w.x + s.w.y * s.w.y + s.w.z * s.w.z;
     float B = s.Y0.x * s.w.x + s.Y0.y * s.w.y + s.Y0.z * s.w.z;
     float y0 = sqrtf(s.Y0.x * s.Y0.x + s.Y0.y * s.Y0.y + s.Y0.z * s.Y0.z);
     float C = (y0 - d) * (y0 + d);
-    float disc = B * B - A * C;
-    if (disc >= 0.0f) {
-        float sq = sqrtf(disc);
-        float q = -(B + copysignf(sq, B));
-        float r1 = q / A, r2 = (q != 0.0f) ? C / q : r1;
-        float lo = fminf(r1, r2), hi = fmaxf(r1, r2);
-        float span = (tb < kInf) ? tb - ta : 0.0f;
-        float slack = 1e-5f * (span + fabsf(ta) + 1e-3f);
-        float tbs = (tb < kInf) ? tb + slack : kInf;
-        if (lo >= ta - slack && lo <= tbs) return fminf(fmaxf(lo, ta), tb);
-        if (hi >= ta - slack && hi <= tbs) return fminf(fmaxf(hi, ta), tb);
+    float sq = sqrtf(fmaxf(B * B - A * C, 0.0f));
+    float t;
+    if (r2_at(s, ta) < d * d) {
+        t = B > 0.0f ? -C / (B + sq) : (sq - B) / A;  // larger root
+    } else {
+        float tstar = -B / A;
+        if (!(tstar > ta)) return ta;
+        if (B * B - A * C < 0.0f) t = tstar;
+        else t = B < 0.0f ? C / (sq - B) : -(B + sq) / A;  // smaller root
     }
-    return ta;
+    return fminf(fmaxf(t, ta), tb);
 }
 
 template <int RADF>

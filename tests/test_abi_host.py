@@ -14,8 +14,8 @@ HEADER = os.path.join(ROOT, "include", "lfp.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2507_14624_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__._cuda_build_module().build()
     from paper_2507_14624_gb300 import lfp
     return lfp
 
