@@ -47,6 +47,7 @@ typedef enum {
     LFP_ERR_OOM = 2,         /* a device allocation failed */
     LFP_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
     LFP_ERR_STATE = 4,       /* call order violated (e.g. render before upload) */
+    LFP_ERR_CAPACITY = 5,    /* request larger than a fixed-size buffer allows */
     LFP_WARN_STEPLIMIT = 100 /* some ray hit the per-ray step cap (class 3) */
 } lfp_status;
 
@@ -198,6 +199,31 @@ lfp_status lfp_check_flags(lfp_grid* grid, void* cuda_stream);
 /* Device bytes the grid's probe storage takes for a descriptor (maps + mip),
  * the byte accounting of Sec. 6 (memory efficient representation). */
 lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes);
+
+/* Most views one lfp_render_static call accepts. */
+#define LFP_STATIC_MAX_VIEWS 4096
+
+/* Forward render that allocates nothing (the paper has no counterpart: this
+ * is an interface for callers that cannot allocate device memory at render
+ * time -- a render recorded during CUDA stream capture, where cudaMalloc is
+ * not allowed; a real-time frame loop that must not touch the allocator after
+ * start-up; a host whose device memory comes from its own fixed-budget
+ * allocator). Same results and outputs as lfp_render_ex with
+ * LFP_SCHED_PERSISTENT and 16x8 ray tiles, in one persistent launch for all
+ * n_views <= LFP_STATIC_MAX_VIEWS views (more -> LFP_ERR_CAPACITY, nothing
+ * is launched). The work-queue head and the view table live in one
+ * file-scope device array of 256 B + LFP_STATIC_MAX_VIEWS * 80 B (about
+ * 320 KiB) that every GPU loading the library keeps until the process exits.
+ *   - The first call on a device sets that device up (looks up the array's
+ *     device address, sizes the persistent grid); make that first call
+ *     before any stream capture.
+ *   - All calls share the array: the queue head is cleared by every call and
+ *     the view table is rewritten, so calls that overlap on the GPU (other
+ *     streams, other host threads) race; serialise them on one stream.
+ *   - `views` is host memory, copied before the call returns.
+ *   - grid: created and uploaded beforehand (those calls do allocate). */
+lfp_status lfp_render_static(lfp_grid* grid, const lfp_view* views, int n_views,
+                             const lfp_outputs* out, void* cuda_stream);
 
 /* Release a grid (NULL-safe; synchronises the device first). */
 void lfp_destroy_grid(lfp_grid* grid);

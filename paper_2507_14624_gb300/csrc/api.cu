@@ -229,6 +229,29 @@ void destroy(lfp_grid* g) {
 
 }  // namespace
 
+namespace lfp {
+
+bool grid_access(const lfp_grid* g, GridAccess* out) {
+    if (!g || !out) return false;
+    out->dev = grid_dev(g);
+    out->rad_fmt = g->desc.radiance_fmt;
+    out->nrm_fmt = g->desc.normal_fmt;
+    out->device = g->device;
+    out->sm_count = g->sm_count;
+    out->all_uploaded = 1;
+    for (unsigned char u : g->uploaded)
+        if (!u) out->all_uploaded = 0;
+    return true;
+}
+
+ViewDev view_dev_of(const lfp_view& v, int tile_w, int tile_h, int tile_begin) {
+    return view_dev(v, tile_w, tile_h, tile_begin);
+}
+
+int check_views_of(const lfp_view* views, int n_views) { return check_views(views, n_views); }
+
+}  // namespace lfp
+
 extern "C" {
 
 const char* lfp_status_string(lfp_status s) {
@@ -238,6 +261,7 @@ const char* lfp_status_string(lfp_status s) {
         case LFP_ERR_OOM: return "out of device memory";
         case LFP_ERR_CUDA: return "CUDA error";
         case LFP_ERR_STATE: return "invalid call order (e.g. probes not uploaded)";
+        case LFP_ERR_CAPACITY: return "request exceeds a fixed-size buffer (e.g. more than LFP_STATIC_MAX_VIEWS views)";
         case LFP_WARN_STEPLIMIT: return "some rays reached the step limit";
     }
     return "unknown status";

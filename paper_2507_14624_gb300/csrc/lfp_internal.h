@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "lfp.h"
 #include "lfp_device.cuh"
 
 namespace lfp {
@@ -25,5 +26,18 @@ cudaError_t launch_build_mip(const float* dist, float2* mip, int count, int N, i
 // adjoint scatter into grad_radiance [P][N][N][3]
 cudaError_t launch_backward(int N, const PixBatch& pb, const float* grad_rgb, const uint8_t* cls,
                             const int32_t* aux_probe, const float* aux_uv, float* grad_rad, cudaStream_t s);
+
+// Read-only access to a grid for render entry points outside api.cu.
+struct GridAccess {
+    GridDev dev;
+    int rad_fmt, nrm_fmt;
+    int device, sm_count;
+    int all_uploaded;
+};
+bool grid_access(const struct lfp_grid* g, GridAccess* out);
+// lfp_view -> kernel view constants (tile_w x tile_h ray tiles)
+ViewDev view_dev_of(const lfp_view& v, int tile_w, int tile_h, int tile_begin);
+// 0 if the views are valid (lfp_status otherwise)
+int check_views_of(const lfp_view* views, int n_views);
 
 }  // namespace lfp

@@ -14,7 +14,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "liblfp.so")
 
 # status codes
-LFP_OK, LFP_ERR_INVALID_ARG, LFP_ERR_OOM, LFP_ERR_CUDA, LFP_ERR_STATE = 0, 1, 2, 3, 4
+LFP_OK, LFP_ERR_INVALID_ARG, LFP_ERR_OOM, LFP_ERR_CUDA, LFP_ERR_STATE, LFP_ERR_CAPACITY = 0, 1, 2, 3, 4, 5
+LFP_STATIC_MAX_VIEWS = 4096
 LFP_WARN_STEPLIMIT = 100
 LFP_TEXEL_F32, LFP_TEXEL_F16 = 0, 1
 LFP_CLASS_MISS, LFP_CLASS_HIT, LFP_CLASS_UNKNOWN, LFP_CLASS_STEPLIMIT = 0, 1, 2, 3
@@ -71,6 +72,7 @@ def _load():
         "lfp_render": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp], i),
         "lfp_render_ex": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
         "lfp_render_to_host": ([vp, P(lfp_view), i, vp, vp, vp], i),
+        "lfp_render_static": ([vp, P(lfp_view), i, P(lfp_outputs), vp], i),
         "lfp_render_backward": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, vp], i),
         "lfp_set_radiance": ([vp, vp, vp], i),
         "lfp_check_flags": ([vp, vp], i),
@@ -119,6 +121,11 @@ def lfp_render(grid, views, n_views, rgb, cls, aux_probe, aux_uv, stream) -> Non
 def lfp_render_ex(grid, views, n_views, outputs: lfp_outputs, opts: lfp_render_opts | None, stream) -> None:
     _check(_lib.lfp_render_ex(grid, views, n_views, ctypes.byref(outputs),
                               ctypes.byref(opts) if opts is not None else None, stream), "lfp_render_ex")
+
+
+def lfp_render_static(grid, views, n_views, outputs: lfp_outputs, stream) -> None:
+    """Forward render that allocates nothing (fixed scratch; see include/lfp.h)."""
+    _check(_lib.lfp_render_static(grid, views, n_views, ctypes.byref(outputs), stream), "lfp_render_static")
 
 
 def lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream) -> None:
