@@ -132,6 +132,7 @@ typedef struct {
 /* Launch options for lfp_render_ex (zero-initialised = defaults). */
 enum { LFP_MARCH_HIER = 0, LFP_MARCH_FLAT = 1 };
 enum { LFP_SCHED_AUTO = 0, LFP_SCHED_TILES = 1, LFP_SCHED_PERSISTENT = 2 };
+enum { LFP_ENGINE_AUTO = 0, LFP_ENGINE_STREAM = 1, LFP_ENGINE_NESTED = 2 };
 typedef struct {
     int march;      /* LFP_MARCH_HIER (low-res then full-res) or LFP_MARCH_FLAT
                        (Appendix A RayMarching over the full-res map only) */
@@ -139,7 +140,13 @@ typedef struct {
                        Valid shapes: 8x4, 8x8, 16x8, 16x16, 32x8 */
     int tile_h;
     int schedule;   /* LFP_SCHED_*: one CTA per tile, or a persistent grid
-                       pulling tiles from a queue */
+                       pulling tiles from a queue (nested engine only) */
+    int engine;     /* LFP_ENGINE_STREAM (default): a persistent per-lane
+                       state machine, one texel visit per lane per step, lanes
+                       refilled from 8x4 ray tiles; LFP_ENGINE_NESTED: the
+                       loop nest of Appendix A, one ray per thread (tile_w,
+                       tile_h, schedule and LFP_MARCH_FLAT apply to it only).
+                       Both give identical results. */
 } lfp_render_opts;
 
 /* Create a grid; allocates the device planes for all nx*ny*nz probes on the

@@ -11,12 +11,14 @@ from __future__ import annotations
 import ctypes
 
 from . import lfp
-from .lfp import (LFP_CLASS_HIT, LFP_CLASS_MISS, LFP_CLASS_STEPLIMIT, LFP_CLASS_UNKNOWN, LFP_MARCH_FLAT,
-                  LFP_MARCH_HIER, LFP_SCHED_PERSISTENT, LFP_SCHED_TILES, LFP_TEXEL_F16, LFP_TEXEL_F32, LfpError)
+from .lfp import (LFP_CLASS_HIT, LFP_CLASS_MISS, LFP_CLASS_STEPLIMIT, LFP_CLASS_UNKNOWN, LFP_ENGINE_NESTED,
+                  LFP_ENGINE_STREAM, LFP_MARCH_FLAT, LFP_MARCH_HIER, LFP_SCHED_PERSISTENT, LFP_SCHED_TILES,
+                  LFP_TEXEL_F16, LFP_TEXEL_F32, LfpError)
 
 __all__ = ["lfp", "ProbeGrid", "make_views", "render", "LfpError", "LFP_TEXEL_F32", "LFP_TEXEL_F16",
            "LFP_CLASS_MISS", "LFP_CLASS_HIT", "LFP_CLASS_UNKNOWN", "LFP_CLASS_STEPLIMIT",
-           "LFP_MARCH_HIER", "LFP_MARCH_FLAT", "LFP_SCHED_TILES", "LFP_SCHED_PERSISTENT"]
+           "LFP_MARCH_HIER", "LFP_MARCH_FLAT", "LFP_SCHED_TILES", "LFP_SCHED_PERSISTENT", "LFP_ENGINE_STREAM",
+           "LFP_ENGINE_NESTED"]
 
 
 def _stream_handle(stream=None):
@@ -105,7 +107,7 @@ class ProbeGrid:
         lfp.lfp_set_radiance(self.handle, ctypes.c_void_p(r.data_ptr()), _stream_handle(stream))
 
     def render(self, views, aux=True, hit_texel=False, counters=False, march=LFP_MARCH_HIER, tile=None,
-               schedule=0, stream=None):
+               schedule=0, engine=0, stream=None):
         """Render views; returns a dict of CUDA tensors: rgb [P,3] f32,
         cls [P] u8, and optionally probe [P] i32, uv [P,2] f32, texel [P] i32,
         counters [8] i64 (see lfp.COUNTER_NAMES)."""
@@ -132,6 +134,7 @@ class ProbeGrid:
         if tile is not None:
             opts.tile_w, opts.tile_h = tile
         opts.schedule = schedule
+        opts.engine = engine
         lfp.lfp_render_ex(self.handle, arr, n, o, opts, _stream_handle(stream))
         return out
 

@@ -33,7 +33,8 @@ struct lfp_grid {
     uint8_t* host_cls = nullptr;
     long long host_pixels = 0;
     std::vector<unsigned char> uploaded;
-    int tile_w = 16, tile_h = 8;        // default ray tile
+    int tile_w = 16, tile_h = 8;        // default ray tile (nested engine)
+    int stream_blocks = 0;              // persistent grid of the stream engine (0 = not sized yet)
     int schedule = LFP_SCHED_TILES;
 };
 
@@ -167,8 +168,10 @@ bool valid_tile(int w, int h) {
 
 lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const OutDev& out,
                        const lfp_render_opts* opts, cudaStream_t s) {
-    int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0;
+    int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0, engine = LFP_ENGINE_STREAM;
     if (opts) {
+        if (opts->engine < LFP_ENGINE_AUTO || opts->engine > LFP_ENGINE_NESTED) return LFP_ERR_INVALID_ARG;
+        if (opts->engine != LFP_ENGINE_AUTO) engine = opts->engine;
         if (opts->tile_w || opts->tile_h) {
             if (!valid_tile(opts->tile_w, opts->tile_h)) return LFP_ERR_INVALID_ARG;
             tw = opts->tile_w;
@@ -182,6 +185,31 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
     for (unsigned char u : g->uploaded)
         if (!u) return LFP_ERR_STATE;
     GridDev gd = grid_dev(g);
+    static thread_local ViewBatch vb;  // ~10 KB: keep it off the host stack
+    if (engine == LFP_ENGINE_STREAM && !flat) {
+        if (g->stream_blocks == 0)
+            g->stream_blocks = std::max(1, render_stream_blocks_per_sm(g->desc.radiance_fmt, g->desc.normal_fmt)) *
+                               g->sm_count;
+        for (int first = 0; first < n_views; first += kMaxViewsPerLaunch) {
+            int n = std::min(kMaxViewsPerLaunch, n_views - first);
+            vb.n = n;
+            vb.tile_w = 8;
+            vb.tile_h = 4;
+            long long tiles = 0;
+            for (int i = 0; i < n; ++i) {
+                const lfp_view& v = views[first + i];
+                vb.v[i] = view_dev(v, 8, 4, (int)tiles);
+                tiles += (long long)vb.v[i].tiles_x * ((v.H + 3) / 4);
+                if (tiles > (1LL << 31) - 1) return LFP_ERR_INVALID_ARG;
+            }
+            vb.total_tiles = (int)tiles;
+            int blocks = (int)std::min<long long>(g->stream_blocks, (tiles + 3) / 4);
+            LFP_CUDA(cudaMemsetAsync(g->tile_counter, 0, sizeof(unsigned), s));
+            LFP_CUDA(launch_render_stream(gd, g->desc.radiance_fmt, g->desc.normal_fmt, vb, out, g->tile_counter,
+                                          blocks, s));
+        }
+        return LFP_OK;
+    }
     RenderLaunch L;
     L.flat = flat;
     L.persistent = sched == LFP_SCHED_PERSISTENT;
@@ -191,7 +219,6 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
         int per_sm = render_max_active_blocks(g->desc.radiance_fmt, g->desc.normal_fmt, tw * th);
         L.persistent_blocks = std::max(1, per_sm) * g->sm_count;
     }
-    static thread_local ViewBatch vb;  // ~10 KB: keep it off the host stack
     for (int first = 0; first < n_views; first += kMaxViewsPerLaunch) {
         int n = std::min(kMaxViewsPerLaunch, n_views - first);
         vb.n = n;

@@ -13,8 +13,8 @@ namespace {
 
 using namespace trace;
 
-template <int RADF, int NRMF, bool COUNT>
-__global__ void __launch_bounds__(256) render_kernel(GridDev g, ViewBatch vb, OutDev out, int flat, int persistent,
+template <int RADF, int NRMF, bool COUNT, bool FLAT>
+__global__ void __launch_bounds__(256) render_kernel(GridDev g, ViewBatch vb, OutDev out, int persistent,
                                                      unsigned* tile_counter) {
     __shared__ int s_tile;
     const int tw = vb.tile_w, th = vb.tile_h;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) render_kernel(GridDev g, ViewBatch vb, Ou
             r.w = make_float3(dx * il, dy * il, dz * il);
             Stats<COUNT> st;
             unsigned cells = 0, probes = 0;
-            PixelResult pr = trace_ray<RADF, NRMF, COUNT>(g, r, flat != 0, st, cells, probes);
+            PixelResult pr = trace_ray<RADF, NRMF, COUNT, FLAT>(g, r, st, cells, probes);
             long long o = v.out_offset + (long long)y * v.W + x;
             if (out.rgb) {
                 out.rgb[3 * o + 0] = pr.rgb.x;
@@ -96,10 +96,12 @@ cudaError_t launch_fmt(const GridDev& g, const ViewBatch& vb, const OutDev& out,
     dim3 block(vb.tile_w * vb.tile_h);
     int blocks = L.persistent ? L.persistent_blocks : vb.total_tiles;
     if (blocks <= 0) return cudaSuccess;
-    if (out.counters)
-        render_kernel<RADF, NRMF, true><<<blocks, block, 0, s>>>(g, vb, out, L.flat, L.persistent, L.tile_counter);
+    if (L.flat)  // diagnostic: full-resolution march only, no counters
+        render_kernel<RADF, NRMF, false, true><<<blocks, block, 0, s>>>(g, vb, out, L.persistent, L.tile_counter);
+    else if (out.counters)
+        render_kernel<RADF, NRMF, true, false><<<blocks, block, 0, s>>>(g, vb, out, L.persistent, L.tile_counter);
     else
-        render_kernel<RADF, NRMF, false><<<blocks, block, 0, s>>>(g, vb, out, L.flat, L.persistent, L.tile_counter);
+        render_kernel<RADF, NRMF, false, false><<<blocks, block, 0, s>>>(g, vb, out, L.persistent, L.tile_counter);
     return cudaGetLastError();
 }
 
@@ -116,13 +118,13 @@ cudaError_t launch_render(const GridDev& g, int rad_fmt, int nrm_fmt, const View
 int render_max_active_blocks(int rad_fmt, int nrm_fmt, int threads) {
     int n = 0;
     if (rad_fmt == kF32 && nrm_fmt == kF32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<kF32, kF32, false>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<kF32, kF32, false, false>, threads, 0);
     else if (rad_fmt == kF16 && nrm_fmt == kF16)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<kF16, kF16, false>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<kF16, kF16, false, false>, threads, 0);
     else if (rad_fmt == kF16)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<kF16, kF32, false>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<kF16, kF32, false, false>, threads, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<kF32, kF16, false>, threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<kF32, kF16, false, false>, threads, 0);
     return n;
 }
 

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) render_table_kernel(GridDev g, const View
             r.w = make_float3(dx * il, dy * il, dz * il);
             Stats<COUNT> st;
             unsigned cells = 0, probes = 0;
-            PixelResult pr = trace_ray<RADF, NRMF, COUNT>(g, r, false, st, cells, probes);
+            PixelResult pr = trace_ray<RADF, NRMF, COUNT, false>(g, r, st, cells, probes);
             long long o = v.out_offset + (long long)y * v.W + x;
             if (out.rgb) {
                 out.rgb[3 * o + 0] = pr.rgb.x;

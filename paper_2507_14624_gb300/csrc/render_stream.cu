@@ -1,0 +1,579 @@
+// Forward render, streaming engine: the per-ray tracer of render_trace.cuh
+// recast as a flat per-lane state machine.
+//
+// The nested formulation (cells -> probes -> segments -> low-res walk ->
+// full-res walk, each a loop with early exits) leaves most lanes of a warp
+// idle: lanes at different depths of the nest execute one after another, and
+// a warp waits for its slowest ray. Here every loop iteration gives each lane
+// one texel visit at whichever level it is on (the low- and full-resolution
+// visits are the same instructions with different operands); the rare
+// transitions (next segment, probe, cell, ray) run in a side branch, and a
+// lane whose ray is done takes the next ray from its warp's pool of 8x4 ray
+// tiles, refilled from a global queue. Results are identical to the nested
+// engine: the same arithmetic decides every texel.
+#include <cuda_runtime.h>
+
+#include "lfp_device.cuh"
+#include "lfp_internal.h"
+#include "render_trace.cuh"
+
+namespace lfp {
+namespace {
+
+using namespace trace;
+
+#ifndef LFP_STREAM_WALK_STEPS
+#define LFP_STREAM_WALK_STEPS 16
+#endif
+#ifndef LFP_STREAM_BATCH_PCT
+#define LFP_STREAM_BATCH_PCT 75
+#endif
+#ifndef LFP_STREAM_MIN_BLOCKS
+#define LFP_STREAM_MIN_BLOCKS 5
+#endif
+constexpr int kStreamThreads = 128;
+constexpr int kWalkSteps = LFP_STREAM_WALK_STEPS;  // texel visits per lane between control rounds
+constexpr int kBatchPct = LFP_STREAM_BATCH_PCT;     // transitions run once this % of busy lanes wait
+constexpr unsigned kFull = 0xffffffffu;
+
+enum Mode : int {
+    kIdle = 0,     // no ray: take one from the pool
+    kWalk,         // one texel visit per iteration
+    kCellStart,    // set up the cage of cell c
+    kProbeStart,   // set up probe of rank q
+    kSegStart,     // set up segment segi of the probe
+    kSegEnd,       // the segment ended without a decision
+    kUnknownRes,   // the probe returned UNKNOWN
+    kNextCell,     // the probe returned MISS, or all 8 were UNKNOWN
+    kRayDone,      // write the pixel
+    kExit          // no rays left
+};
+
+// Per-lane state, kept in registers (no member is indexed at run time).
+struct Lane {
+    int mode;
+    float3 X, w;         // the ray
+    long long o;         // output index
+    int c0, c1, c2;      // current cell
+    int cbits;           // step signs (2 bits per axis: 1 +, 2 -), bits 6-7 exit axis,
+                         // bit 8 last cell, bit 9 saw UNKNOWN
+    float t_in, t_out;
+    unsigned order;      // cage order: corner of rank q in bits [3q, 3q + 3)
+    int q, kq, probe;    // rank, corner bits and index of the current probe
+    float cut0, cut1, cut2, seg_a, seg_b;
+    int segi, seg_final;
+    // segment (see Seg): u-parametrised octant line
+    float3 Ya;
+    float cp, e, m0, m1, q0, q1, p00, p01, k0, k1, A0, A1, A2, u_end, tstar;
+    int dir0, dir1;
+    int quad;            // bit a set: the segment's octant has p_a >= 0
+    const float* dmap;   // this probe's distance map
+    const float2* mmap;  // this probe's min/max map
+    // walk
+    int level, i, j, lo0, hi0, lo1, hi1;
+    float ux, uy, u, u1, Pa, D2a;  // after a HIT: (ux, uy) hold the shading uv
+    int I, J, lastc;
+    float uxc, uyc, uec;
+    int cls;
+};
+
+__device__ __forceinline__ int step_of(int bits, int a) {
+    int v = (bits >> (2 * a)) & 3;
+    return v == 1 ? 1 : (v == 2 ? -1 : 0);
+}
+
+// Grid-iterator set-up for a new ray; returns false if it misses the grid.
+__device__ __forceinline__ bool ray_enter_grid(const GridDev& g, Lane& L) {
+    const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
+    const float og[3] = {g.ox, g.oy, g.oz};
+    const float Xa[3] = {L.X.x, L.X.y, L.X.z}, Wa[3] = {L.w.x, L.w.y, L.w.z};
+    float t_enter = 0.0f, t_exit = kInf;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float lo = grid_plane(og[a], g.spacing, 0), hi = grid_plane(og[a], g.spacing, nc[a]);
+        if (Wa[a] == 0.0f) {
+            if (Xa[a] < lo || Xa[a] > hi) t_enter = kInf;
+            continue;
+        }
+        float ta = (lo - Xa[a]) / Wa[a], tb = (hi - Xa[a]) / Wa[a];
+        if (ta > tb) { float x = ta; ta = tb; tb = x; }
+        t_enter = fmaxf(t_enter, ta);
+        t_exit = fminf(t_exit, tb);
+    }
+    if (!(t_enter <= t_exit)) return false;
+    int c[3], bits = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float p = fmaf(t_enter, Wa[a], Xa[a]);
+        c[a] = min(max((int)floorf((p - og[a]) / g.spacing), 0), nc[a] - 1);
+        bits |= (Wa[a] > 0.0f ? 1 : (Wa[a] < 0.0f ? 2 : 0)) << (2 * a);
+    }
+    L.c0 = c[0];
+    L.c1 = c[1];
+    L.c2 = c[2];
+    L.cbits = bits;
+    L.t_in = 0.0f;
+    return true;
+}
+
+// Cell c: its exit (3D DDA) and its cage order, nearest corner to the entry first.
+__device__ __forceinline__ void cell_start(const GridDev& g, Lane& L) {
+    const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
+    const float og[3] = {g.ox, g.oy, g.oz};
+    const float Xa[3] = {L.X.x, L.X.y, L.X.z}, Wa[3] = {L.w.x, L.w.y, L.w.z};
+    const int c[3] = {L.c0, L.c1, L.c2};
+    float tm[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int st = step_of(L.cbits, a);
+        tm[a] = st == 0 ? kInf
+                        : (grid_plane(og[a], g.spacing, c[a] + (st > 0 ? 1 : 0)) - Xa[a]) * __frcp_rn(Wa[a]);
+    }
+    int ax = 0;
+    if (tm[1] < tm[ax]) ax = 1;
+    if (tm[2] < tm[ax]) ax = 2;
+    int st = step_of(L.cbits, ax);
+    int cax = ax == 0 ? c[0] : (ax == 1 ? c[1] : c[2]);
+    int ncax = ax == 0 ? nc[0] : (ax == 1 ? nc[1] : nc[2]);
+    int nxt = cax + st;
+    bool last = st == 0 || nxt < 0 || nxt > ncax - 1;
+    float tax = ax == 0 ? tm[0] : (ax == 1 ? tm[1] : tm[2]);
+    L.cbits = (L.cbits & 0x23f) | (ax << 6) | (last ? 0x100 : 0);
+    L.t_out = last ? kInf : tax;
+    float3 P = make_float3(fmaf(L.t_in, L.w.x, L.X.x), fmaf(L.t_in, L.w.y, L.X.y), fmaf(L.t_in, L.w.z, L.X.z));
+    L.order = cage_order(g, L.c0, L.c1, L.c2, P);
+    L.q = 0;
+}
+
+// Probe of rank q: its index and the cut points of the octant split.
+__device__ __forceinline__ void probe_start(const GridDev& g, Lane& L) {
+    L.kq = (L.order >> (3 * L.q)) & 7;
+    L.probe = corner_index(g, L.c0, L.c1, L.c2, L.kq);
+    float3 O = corner_pos(g, L.c0, L.c1, L.c2, L.kq);
+    const float t0 = L.t_in, t1 = L.t_out;
+    float cx = L.w.x != 0.0f ? (O.x - L.X.x) * __frcp_rn(L.w.x) : kInf;
+    float cy = L.w.y != 0.0f ? (O.y - L.X.y) * __frcp_rn(L.w.y) : kInf;
+    float cz = L.w.z != 0.0f ? (O.z - L.X.z) * __frcp_rn(L.w.z) : kInf;
+    cx = (cx > t0 && cx < t1) ? cx : kInf;
+    cy = (cy > t0 && cy < t1) ? cy : kInf;
+    cz = (cz > t0 && cz < t1) ? cz : kInf;
+    L.cut0 = fminf(cx, fminf(cy, cz));
+    L.cut2 = fmaxf(cx, fmaxf(cy, cz));
+    L.cut1 = fmaxf(fminf(cx, cy), fminf(fmaxf(cx, cy), cz));
+    L.segi = 0;
+    L.seg_a = t0;
+}
+
+// Low-resolution index box of the segment's quadrant.
+__device__ __forceinline__ void coarse_box(const GridDev& g, Lane& L) {
+    const int hm = g.M / 2;
+    L.lo0 = (L.quad & 1) ? hm : 0;
+    L.hi0 = (L.quad & 1) ? g.M - 1 : hm - 1;
+    L.lo1 = (L.quad & 2) ? hm : 0;
+    L.hi1 = (L.quad & 2) ? g.M - 1 : hm - 1;
+}
+
+// Segment segi: the octant line (same arithmetic as seg_setup) and the
+// start of the low-resolution walk.
+__device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
+    float b = L.segi == 0 ? L.cut0 : (L.segi == 1 ? L.cut1 : (L.segi == 2 ? L.cut2 : kInf));
+    L.seg_final = !(b < kInf);
+    if (L.seg_final) b = L.t_out;
+    L.seg_b = b;
+    float3 O = corner_pos(g, L.c0, L.c1, L.c2, L.kq);
+    Seg s;
+    seg_setup(s, make_float3(L.X.x - O.x, L.X.y - O.y, L.X.z - O.z), L.w, L.seg_a, b, g.N);
+    L.Ya = s.Ya;
+    L.cp = s.cp;
+    L.e = s.e;
+    L.m0 = s.m[0];
+    L.m1 = s.m[1];
+    L.q0 = s.q[0];
+    L.q1 = s.q[1];
+    L.p00 = s.p0[0];
+    L.p01 = s.p0[1];
+    L.k0 = s.k[0];
+    L.k1 = s.k[1];
+    L.A0 = s.A0;
+    L.A1 = s.A1;
+    L.A2 = s.A2;
+    L.u_end = s.u_end;
+    L.tstar = s.tstar;
+    L.dir0 = s.dir[0];
+    L.dir1 = s.dir[1];
+    L.quad = (s.lo[0] > 0 ? 1 : 0) | (s.lo[1] > 0 ? 2 : 0);
+    L.dmap = g.dist + (size_t)L.probe * g.N * g.N;
+    L.mmap = g.mip + (size_t)L.probe * g.M * g.M;
+    const int k = g.k, N = g.N;
+    L.level = 0;
+    coarse_box(g, L);
+    L.i = min(max(texel_of(L.p00, N, L.dir0) / k, L.lo0), L.hi0);
+    L.j = min(max(texel_of(L.p01, N, L.dir1) / k, L.lo1), L.hi1);
+    L.u = 0.0f;
+    L.u1 = L.u_end;
+    L.Pa = L.A0;
+    L.D2a = 1.0f;
+    L.ux = L.dir0 == 0 ? kInf : fmaxf(fmaf((float)((L.dir0 > 0 ? L.i + 1 : L.i) * k), L.m0, L.q0), 0.0f);
+    L.uy = L.dir1 == 0 ? kInf : fmaxf(fmaf((float)((L.dir1 > 0 ? L.j + 1 : L.j) * k), L.m1, L.q1), 0.0f);
+}
+
+// tau from the segment start of walk parameter u (infinite past the end)
+__device__ __forceinline__ float lane_tau(const Lane& L, float u) {
+    float D = fmaf(-L.e, u, 1.0f);
+    return D > 0.0f ? L.cp * u / D : kInf;
+}
+
+__device__ __forceinline__ float lane_r2(const Lane& L, float tau) {
+    float x = fmaf(tau, L.w.x, L.Ya.x), y = fmaf(tau, L.w.y, L.Ya.y), z = fmaf(tau, L.w.z, L.Ya.z);
+    return x * x + y * y + z * z;
+}
+
+// Advance past the current texel (exit ue) over the earlier next boundary;
+// false when the walk leaves the current level's index box.
+__device__ __forceinline__ bool advance(Lane& L, int scale, float ue, float Pb, float D2b) {
+    if (L.ux <= L.uy) {
+        L.i += L.dir0;
+        if (L.i < L.lo0 || L.i > L.hi0) return false;
+        L.ux = fmaxf(fmaf((float)((L.dir0 > 0 ? L.i + 1 : L.i) * scale), L.m0, L.q0), ue);
+    } else {
+        L.j += L.dir1;
+        if (L.j < L.lo1 || L.j > L.hi1) return false;
+        L.uy = fmaxf(fmaf((float)((L.dir1 > 0 ? L.j + 1 : L.j) * scale), L.m1, L.q1), ue);
+    }
+    L.u = ue;
+    L.Pa = Pb;
+    L.D2a = D2b;
+    return true;
+}
+
+// The full-resolution walk under a low-resolution texel ended without a
+// decision: continue the low-resolution walk after that texel.
+__device__ __forceinline__ void ascend(const GridDev& g, Lane& L) {
+    L.level = 0;
+    L.i = L.I;
+    L.j = L.J;
+    coarse_box(g, L);
+    L.ux = L.uxc;
+    L.uy = L.uyc;
+    L.u1 = L.u_end;
+    float ue = L.uec;
+    float Pb = fmaf(fmaf(L.A2, ue, L.A1), ue, L.A0);
+    float Db = fmaf(-L.e, ue, 1.0f);
+    if (L.lastc || !advance(L, g.k, ue, Pb, Db * Db)) L.mode = kSegEnd;
+}
+
+// One texel visit (Appendix A low/highResolutionTracing, one step).
+template <int NRMF, bool COUNT>
+__device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT>& st) {
+    const int N = g.N, M = g.M, k = g.k;
+    float un = fminf(L.ux, L.uy);
+    bool last = !(un < L.u1);
+    float ue = last ? L.u1 : un;
+    float Pb = fmaf(fmaf(L.A2, ue, L.A1), ue, L.A0);
+    float Db = fmaf(-L.e, ue, 1.0f);
+    float D2b = Db * Db;
+    float v, vmax = 0.0f;
+    if (L.level) {
+        v = __ldg(L.dmap + (L.j * N + L.i));
+        if (COUNT) st.fine++;
+    } else {
+        float2 mm = __ldg(L.mmap + (L.j * M + L.i));
+        v = mm.x;
+        vmax = mm.y;
+        if (COUNT) st.coarse++;
+    }
+    st.steps++;
+    if (g.max_steps > 0 && (int)st.steps >= g.max_steps) {
+        L.cls = kStepLimit;
+        L.mode = kRayDone;
+        return;
+    }
+    float d2 = v * v;
+    if (L.Pa < d2 * L.D2a && Pb < d2 * D2b) {  // the ray stays in front of the stored surface
+        if (!last && advance(L, L.level ? 1 : k, ue, Pb, D2b)) return;
+        if (L.level) ascend(g, L);
+        else L.mode = kSegEnd;
+        return;
+    }
+    if (L.level == 0) {  // candidate low-resolution texel
+        if (!g.two_way) {
+            float ta = lane_tau(L, L.u), tb = lane_tau(L, ue);
+            float dk = vmax * g.kappa;
+            if (lane_r2(L, fminf(fmaxf(L.tstar, ta), tb)) > dk * dk) {
+                L.mode = kUnknownRes;  // every full-resolution texel under it is passed behind
+                return;
+            }
+        }
+        L.I = L.i;
+        L.J = L.j;
+        L.uxc = L.ux;
+        L.uyc = L.uy;
+        L.uec = ue;
+        L.lastc = last;
+        L.level = 1;
+        L.lo0 = L.I * k;
+        L.hi0 = L.lo0 + k - 1;
+        L.lo1 = L.J * k;
+        L.hi1 = L.lo1 + k - 1;
+        L.u1 = ue;
+        L.i = min(max(texel_of(fmaf(L.k0, L.u, L.p00), N, L.dir0), L.lo0), L.hi0);
+        L.j = min(max(texel_of(fmaf(L.k1, L.u, L.p01), N, L.dir1), L.lo1), L.hi1);
+        L.ux = L.dir0 == 0 ? kInf : fmaxf(fmaf((float)(L.dir0 > 0 ? L.i + 1 : L.i), L.m0, L.q0), L.u);
+        L.uy = L.dir1 == 0 ? kInf : fmaxf(fmaf((float)(L.dir1 > 0 ? L.j + 1 : L.j), L.m1, L.q1), L.u);
+        return;
+    }
+    // full-resolution crossing: the normal decides (highResolutionTracing)
+    float ta = lane_tau(L, L.u), tb = lane_tau(L, ue);
+    float d = v, dk = d * g.kappa;
+    L.mode = kUnknownRes;
+    if (g.two_way || lane_r2(L, fminf(fmaxf(L.tstar, ta), tb)) <= dk * dk) {
+        float2 no = NrmTexel<NRMF>::load(g.nrm, (size_t)L.probe * N * N + (size_t)L.j * N + L.i);
+        float3 n = oct_decode_unnorm(no.x, no.y);
+        if (COUNT) st.normal++;
+        if ((n.x * L.w.x + n.y * L.w.y + n.z * L.w.z) < 0.0f) {
+            Seg s;  // the hit point needs Ya, w and |Ya|^2 only
+            s.Ya = L.Ya;
+            s.w = L.w;
+            s.A0 = L.A0;
+            float th = hit_time(s, ta, tb, d);
+            float2 pp = oct_encode(fmaf(th, L.w.x, L.Ya.x), fmaf(th, L.w.y, L.Ya.y), fmaf(th, L.w.z, L.Ya.z));
+            L.cls = kHit;
+            L.ux = 0.5f * (pp.x + 1.0f);  // shading uv
+            L.uy = 0.5f * (pp.y + 1.0f);
+            L.mode = kRayDone;
+        }
+    }
+}
+
+// Start the ray of slot `slot` (0..31) of 8x4 ray tile `tile`.
+__device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb, int tile, int slot, Lane& L) {
+    int lo = 0, hi = vb.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (vb.v[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+    }
+    const ViewDev& v = vb.v[lo];
+    int lt = tile - v.tile_begin;
+    int x = (lt % v.tiles_x) * 8 + (slot & 7), y = (lt / v.tiles_x) * 4 + (slot >> 3);
+    if (x >= v.W || y >= v.H) {
+        L.mode = kIdle;  // outside a ragged view: no ray in this slot
+        return;
+    }
+    float a = ((x + 0.5f) / (float)v.W * 2.0f - 1.0f) * v.sa;
+    float b = (1.0f - (y + 0.5f) / (float)v.H * 2.0f) * v.sb;
+    float dx = v.fx + a * v.rx + b * v.ux, dy = v.fy + a * v.ry + b * v.uy, dz = v.fz + a * v.rz + b * v.uz;
+    float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    L.X = make_float3(v.px, v.py, v.pz);
+    L.w = make_float3(dx * il, dy * il, dz * il);
+    L.o = v.out_offset + (long long)y * v.W + x;
+    L.cls = kMiss;
+    // eye aligned with a probe (Sec. 4.2): the nearest grid vertex within
+    // eye_eps is looked up at oct(w) directly
+    const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
+    const float og[3] = {g.ox, g.oy, g.oz}, Xa[3] = {L.X.x, L.X.y, L.X.z};
+    int iv[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) iv[q] = min(max((int)rintf((Xa[q] - og[q]) / g.spacing), 0), nc[q]);
+    int p = iv[0] + g.nx * (iv[1] + g.ny * iv[2]);
+    float3 O = corner_pos(g, iv[0], iv[1], iv[2], 0);
+    float ex = L.X.x - O.x, ey = L.X.y - O.y, ez = L.X.z - O.z;
+    if (sqrtf(ex * ex + ey * ey + ez * ez) < g.eye_eps) {
+        float2 pp = oct_encode(L.w.x, L.w.y, L.w.z);
+        L.cls = kHit;
+        L.probe = p;
+        L.ux = 0.5f * (pp.x + 1.0f);
+        L.uy = 0.5f * (pp.y + 1.0f);
+        L.i = texel_of(pp.x, g.N, 1);
+        L.j = texel_of(pp.y, g.N, 1);
+        L.mode = kRayDone;
+        return;
+    }
+    L.mode = ray_enter_grid(g, L) ? kCellStart : kRayDone;
+}
+
+template <int RADF>
+__device__ __forceinline__ void write_ray(const GridDev& g, const OutDev& out, const Lane& L) {
+    const long long o = L.o;
+    const bool hit = L.cls == kHit;
+    float3 rgb = make_float3(0.f, 0.f, 0.f);
+    if (hit) rgb = shade<RADF>(g, L.probe, L.ux, L.uy);
+    if (out.rgb) {
+        out.rgb[3 * o + 0] = rgb.x;
+        out.rgb[3 * o + 1] = rgb.y;
+        out.rgb[3 * o + 2] = rgb.z;
+    }
+    if (out.cls) out.cls[o] = (uint8_t)L.cls;
+    if (out.aux_probe) out.aux_probe[o] = hit ? L.probe : -1;
+    if (out.aux_uv) {
+        out.aux_uv[2 * o + 0] = hit ? L.ux : 0.0f;
+        out.aux_uv[2 * o + 1] = hit ? L.uy : 0.0f;
+    }
+    if (out.hit_texel) out.hit_texel[o] = hit ? L.i + g.N * L.j : -1;
+    if (L.cls == kStepLimit) atomicOr(g.flags, 1u);
+}
+
+// Persistent kernel: every warp pulls 8x4 ray tiles from `queue` and keeps
+// its 32 lanes busy, one texel visit per lane per iteration.
+template <int RADF, int NRMF, bool COUNT>
+__global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_stream_kernel(GridDev g, ViewBatch vb, OutDev out,
+                                                                          unsigned* queue) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    Lane L;
+    L.mode = kIdle;
+    Stats<COUNT> st;
+    unsigned cells = 0, probes = 0;
+    unsigned long long acc[kNumCounters];
+    if (COUNT)
+        for (int q = 0; q < kNumCounters; ++q) acc[q] = 0;
+    int pool_tile = 0, pool_next = 32;  // warp-uniform ray pool: one 8x4 tile
+    bool exhausted = false;
+    for (;;) {
+        // refill idle lanes from the warp's pool (warp-synchronous)
+        unsigned idle = __ballot_sync(kFull, L.mode == kIdle);
+        while (idle != 0u && !exhausted) {
+            if (pool_next >= 32) {
+                int t = 0;
+                if (lane == 0) t = (int)atomicAdd(queue, 1u);
+                t = __shfl_sync(kFull, t, 0);
+                if (t >= vb.total_tiles) {
+                    exhausted = true;
+                    break;
+                }
+                pool_tile = t;
+                pool_next = 0;
+            }
+            int avail = 32 - pool_next;
+            int rank = __popc(idle & lanes_below);
+            if (L.mode == kIdle && rank < avail) {
+                st = Stats<COUNT>();
+                cells = probes = 0;
+                start_ray(g, vb, pool_tile, pool_next + rank, L);
+            }
+            pool_next += min(__popc(idle), avail);
+            idle = __ballot_sync(kFull, L.mode == kIdle);
+        }
+        if (exhausted && L.mode == kIdle) L.mode = kExit;
+        if (__all_sync(kFull, L.mode == kExit)) break;
+
+        // Transitions are expensive and divergent: a lane that needs one waits
+        // until kBatchPct % of the busy lanes do (or none walks), so the
+        // set-up code runs for many lanes at once.
+        const bool pending = L.mode != kWalk && L.mode != kIdle && L.mode != kExit;
+        const unsigned pend = __ballot_sync(kFull, pending);
+        const unsigned walk = __ballot_sync(kFull, L.mode == kWalk);
+        if (walk != 0u && 100 * __popc(pend) < kBatchPct * __popc(pend | walk)) {
+#pragma unroll 1
+            for (int r = 0; r < kWalkSteps && L.mode == kWalk; ++r) walk_step<NRMF, COUNT>(g, L, st);
+            continue;
+        }
+
+        // transitions: chain until the lane walks again or its ray is done
+        while (L.mode != kWalk && L.mode != kIdle && L.mode != kExit) {
+            switch (L.mode) {
+                case kCellStart:
+                    ++cells;
+                    cell_start(g, L);
+                    L.mode = kProbeStart;
+                    break;
+                case kProbeStart:
+                    ++probes;
+                    probe_start(g, L);
+                    L.mode = kSegStart;
+                    break;
+                case kSegStart:
+                    seg_start(g, L);
+                    L.mode = kWalk;
+                    break;
+                case kSegEnd:  // MISS on this segment: next segment, or the probe is a MISS
+                    if (L.seg_final) {
+                        L.mode = kNextCell;
+                    } else {
+                        ++L.segi;
+                        L.seg_a = L.seg_b;
+                        L.mode = kSegStart;
+                    }
+                    break;
+                case kUnknownRes:  // UNKNOWN falls through to the next probe of the cage
+                    if (++L.q == 8) {
+                        L.cbits |= 0x200;  // saw UNKNOWN
+                        L.mode = kNextCell;
+                    } else {
+                        L.mode = kProbeStart;
+                    }
+                    break;
+                case kNextCell:
+                    if (L.cbits & 0x100) {  // last cell
+                        L.cls = (L.cbits & 0x200) ? kUnknown : kMiss;
+                        L.mode = kRayDone;
+                    } else {
+                        int ax = (L.cbits >> 6) & 3;
+                        int st_ax = step_of(L.cbits, ax);
+                        if (ax == 0) L.c0 += st_ax;
+                        else if (ax == 1) L.c1 += st_ax;
+                        else L.c2 += st_ax;
+                        L.t_in = L.t_out;
+                        L.mode = kCellStart;
+                    }
+                    break;
+                default:  // kRayDone
+                    write_ray<RADF>(g, out, L);
+                    if (COUNT) {
+                        acc[0] += st.coarse;
+                        acc[1] += st.fine;
+                        acc[2] += st.normal;
+                        acc[3] += L.cls == kHit ? 4 : 0;
+                        const bool eye = L.cls == kHit && cells == 0;  // eye-aligned lookup
+                        acc[4] += eye ? 1 : cells;
+                        acc[5] += eye ? 1 : probes;
+                        acc[6] += L.cls == kHit ? 1 : 0;
+                        acc[7] += 1;
+                    }
+                    L.mode = kIdle;
+                    break;
+            }
+        }
+    }
+    if (COUNT) {
+        for (int q = 0; q < kNumCounters; ++q) {
+            unsigned long long v = acc[q];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
+            if (lane == 0 && v) atomicAdd(out.counters + q, v);
+        }
+    }
+}
+
+template <int RADF, int NRMF>
+cudaError_t launch_stream_fmt(const GridDev& g, const ViewBatch& vb, const OutDev& out, unsigned* queue, int blocks,
+                              cudaStream_t s) {
+    if (out.counters)
+        render_stream_kernel<RADF, NRMF, true><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+    else
+        render_stream_kernel<RADF, NRMF, false><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_render_stream(const GridDev& g, int rad_fmt, int nrm_fmt, const ViewBatch& vb, const OutDev& out,
+                                 unsigned* queue, int blocks, cudaStream_t s) {
+    if (rad_fmt == kF32 && nrm_fmt == kF32) return launch_stream_fmt<kF32, kF32>(g, vb, out, queue, blocks, s);
+    if (rad_fmt == kF16 && nrm_fmt == kF16) return launch_stream_fmt<kF16, kF16>(g, vb, out, queue, blocks, s);
+    if (rad_fmt == kF16 && nrm_fmt == kF32) return launch_stream_fmt<kF16, kF32>(g, vb, out, queue, blocks, s);
+    return launch_stream_fmt<kF32, kF16>(g, vb, out, queue, blocks, s);
+}
+
+int render_stream_blocks_per_sm(int rad_fmt, int nrm_fmt) {
+    int n = 0;
+    if (rad_fmt == kF32 && nrm_fmt == kF32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<kF32, kF32, false>, kStreamThreads, 0);
+    else if (rad_fmt == kF16 && nrm_fmt == kF16)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<kF16, kF16, false>, kStreamThreads, 0);
+    else if (rad_fmt == kF16)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<kF16, kF32, false>, kStreamThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<kF32, kF16, false>, kStreamThreads, 0);
+    return n;
+}
+
+}  // namespace lfp

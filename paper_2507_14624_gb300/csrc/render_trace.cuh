@@ -31,42 +31,33 @@ struct Ray {
     float3 X, w;
 };
 
+// One octant segment [ta, tb] of the ray relative to a probe, walked in the
+// projective parameter u = tau / (c + e tau), tau = t - ta: inside an octant
+// the octahedral coordinates p_a = (alpha_a + beta_a tau) / (c + e tau) are
+// affine in u, p_a = p0_a + k_a u, so the crossing of texel boundary b
+// (p = 2 b / N - 1) is u = b m_a + q_a, one multiply-add. The radial test
+// r(tau) < d becomes |Ya + u V|^2 < d^2 (1 - e u)^2 with V = c w - e Ya
+// (because Ya + tau w = (Ya + u V) / (1 - e u)): no division per texel.
 struct Seg {
-    float3 Y0;         // X - O
+    float3 Ya;         // X + ta w - O
     float3 w;
-    float tstar;       // closest approach of the ray to the probe
-    float c, e;        // denominator c + e t (the octant's L1 norm)
-    float al[2], be[2];// numerators alpha + beta t
-    int dir[2];        // motion of p_x, p_y along the segment
+    float cp, e;       // L1 norm of the octant along the segment: cp + e tau, cp > 0
+    float m[2], q[2];  // boundary crossing u = b m + q (full-resolution b)
+    float p0[2], k[2]; // p_a(u) = p0 + k u
+    float A0, A1, A2;  // |Ya + u V|^2 = A0 + u (A1 + u A2)
+    float u_end;
+    float tstar;       // closest approach to the probe (tau)
+    int dir[2];        // motion of p_x, p_y with u
     int lo[2], hi[2];  // quadrant of the square (full-resolution indices)
 };
 
 struct Decision {
     int cls;           // kMiss / kHit / kUnknown
-    int i, j;          // deciding full-resolution texel (HIT)
-    float ta, tb, d;   // its interval and stored distance (HIT)
+    int texel;         // deciding full-resolution texel i + N j (HIT)
+    float u, v;        // shading coordinate in [0,1]^2 (HIT)
 };
 
-__device__ __forceinline__ float r2_at(const Seg& s, float t) {
-    if (!(t < kInf)) return kInf;
-    float x = fmaf(t, s.w.x, s.Y0.x), y = fmaf(t, s.w.y, s.Y0.y), z = fmaf(t, s.w.z, s.Y0.z);
-    return x * x + y * y + z * z;
-}
-
-__device__ __forceinline__ float boundary(const Seg& s, int b, int N) {
-    return __fdiv_rn(2.0f * (float)b, (float)N) - 1.0f;
-}
-
-// time at which p_a reaches B, or +inf if it never does on this branch
-__device__ __forceinline__ float cross_time(const Seg& s, int a, float B, float tnow) {
-    float den = s.be[a] - B * s.e;
-    float t = (B * s.c - s.al[a]) / den;
-    if (!(fabsf(t) < kInf)) return kInf;
-    if (!(s.c + s.e * t > 0.0f)) return kInf;
-    return fmaxf(t, tnow);
-}
-
-// full-resolution texel index of p along axis a for a walk moving in dir
+// full-resolution texel index of p along an axis for a walk moving in dir
 __device__ __forceinline__ int texel_of(float p, int N, int dir) {
     float u = (p + 1.0f) * 0.5f * (float)N;
     int i = dir >= 0 ? (int)floorf(u) : (int)ceilf(u) - 1;
@@ -74,31 +65,89 @@ __device__ __forceinline__ int texel_of(float p, int N, int dir) {
 }
 
 __device__ __forceinline__ void seg_setup(Seg& s, float3 Y0, float3 w, float ta, float tb, int N) {
-    s.Y0 = Y0;
+    float3 Ya = make_float3(fmaf(ta, w.x, Y0.x), fmaf(ta, w.y, Y0.y), fmaf(ta, w.z, Y0.z));
+    s.Ya = Ya;
     s.w = w;
-    s.tstar = -(Y0.x * w.x + Y0.y * w.y + Y0.z * w.z) / (w.x * w.x + w.y * w.y + w.z * w.z);
-    float tm = (tb < kInf) ? 0.5f * (ta + tb) : ta + 1.0f;
-    float ym[3] = {fmaf(tm, w.x, Y0.x), fmaf(tm, w.y, Y0.y), fmaf(tm, w.z, Y0.z)};
-    float sg[3] = {sgn_nz(ym[0]), sgn_nz(ym[1]), sgn_nz(ym[2])};
-    float y0[3] = {Y0.x, Y0.y, Y0.z}, ww[3] = {w.x, w.y, w.z};
-    s.c = sg[0] * y0[0] + sg[1] * y0[1] + sg[2] * y0[2];
-    s.e = sg[0] * ww[0] + sg[1] * ww[1] + sg[2] * ww[2];
-    int h = N / 2;
+    float tm = (tb < kInf) ? 0.5f * (tb - ta) : 1.0f;
+    float sg[3] = {sgn_nz(fmaf(tm, w.x, Ya.x)), sgn_nz(fmaf(tm, w.y, Ya.y)), sgn_nz(fmaf(tm, w.z, Ya.z))};
+    float ya[3] = {Ya.x, Ya.y, Ya.z}, ww[3] = {w.x, w.y, w.z};
+    float cp = sg[0] * ya[0] + sg[1] * ya[1] + sg[2] * ya[2];
+    float e = sg[0] * ww[0] + sg[1] * ww[1] + sg[2] * ww[2];
+    cp = fmaxf(cp, 1e-30f);  // the ray starts on the probe only in degenerate cases
+    s.cp = cp;
+    s.e = e;
+    const int h = N / 2;
+    const float two_n = 2.0f / (float)N;
+    const float icp = __frcp_rn(cp);
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
+        float al, be;
         if (sg[2] > 0.0f) {
-            s.al[a] = y0[a];
-            s.be[a] = ww[a];
+            al = ya[a];
+            be = ww[a];
         } else {  // folded lower octant: p_a = (Y_a + s_a s_z Y_z) / |Y|_1
             float f = sg[a] * sg[2];
-            s.al[a] = y0[a] + f * y0[2];
-            s.be[a] = ww[a] + f * ww[2];
+            al = ya[a] + f * ya[2];
+            be = ww[a] + f * ww[2];
         }
-        float slope = s.be[a] * s.c - s.al[a] * s.e;
-        s.dir[a] = slope > 0.0f ? 1 : (slope < 0.0f ? -1 : 0);
+        float p0 = al * icp;
+        float k = (be * cp - al * e) * icp;
+        float ik = __frcp_rn(k);
+        s.p0[a] = p0;
+        s.k[a] = k;
+        s.dir[a] = k > 0.0f ? 1 : (k < 0.0f ? -1 : 0);
+        s.m[a] = two_n * ik;
+        s.q[a] = -(1.0f + p0) * ik;
         s.lo[a] = sg[a] > 0.0f ? h : 0;
         s.hi[a] = sg[a] > 0.0f ? N - 1 : h - 1;
     }
+    float3 V = make_float3(cp * w.x - e * Ya.x, cp * w.y - e * Ya.y, cp * w.z - e * Ya.z);
+    s.A0 = Ya.x * Ya.x + Ya.y * Ya.y + Ya.z * Ya.z;
+    s.A1 = 2.0f * (Ya.x * V.x + Ya.y * V.y + Ya.z * V.z);
+    s.A2 = V.x * V.x + V.y * V.y + V.z * V.z;
+    float te = tb - ta;
+    s.u_end = (te < kInf) ? te * __frcp_rn(fmaf(e, te, cp)) : __frcp_rn(e);
+    s.tstar = -(Ya.x * w.x + Ya.y * w.y + Ya.z * w.z) * __frcp_rn(w.x * w.x + w.y * w.y + w.z * w.z);
+}
+
+// u of the next boundary crossed along axis a from index i (full resolution)
+__device__ __forceinline__ float next_cross(const Seg& s, int a, int i, float u_now) {
+    if (s.dir[a] == 0) return kInf;
+    int b = s.dir[a] > 0 ? i + 1 : i;
+    return fmaxf(fmaf((float)b, s.m[a], s.q[a]), u_now);
+}
+
+__device__ __forceinline__ float tau_of(const Seg& s, float u) {
+    float D = fmaf(-s.e, u, 1.0f);
+    return D > 0.0f ? s.cp * u / D : kInf;
+}
+
+__device__ __forceinline__ float r2_tau(const Seg& s, float tau) {
+    float x = fmaf(tau, s.w.x, s.Ya.x), y = fmaf(tau, s.w.y, s.Ya.y), z = fmaf(tau, s.w.z, s.Ya.z);
+    return x * x + y * y + z * z;
+}
+
+// Hit point (tau from the segment start): the first tau >= ta with
+// |Ya + tau w| = d, clamped to [ta, tb]; when the ray is behind the stored
+// surface at ta it is the smaller root if the ray comes back to d, else the
+// closest approach (ta when receding). |Ya + tau w|^2 = d^2 is
+// A tau^2 + 2 B tau + C = 0; the roots use the cancellation-free forms.
+__device__ __forceinline__ float hit_time(const Seg& s, float ta, float tb, float d) {
+    float A = s.w.x * s.w.x + s.w.y * s.w.y + s.w.z * s.w.z;
+    float B = s.Ya.x * s.w.x + s.Ya.y * s.w.y + s.Ya.z * s.w.z;
+    float y0 = sqrtf(s.A0);
+    float C = (y0 - d) * (y0 + d);
+    float sq = sqrtf(fmaxf(B * B - A * C, 0.0f));
+    float t;
+    if (r2_tau(s, ta) < d * d) {
+        t = B > 0.0f ? -C / (B + sq) : (sq - B) / A;  // larger root
+    } else {
+        float tstar = -B / A;
+        if (!(tstar > ta)) return ta;
+        if (B * B - A * C < 0.0f) t = tstar;
+        else t = B < 0.0f ? C / (sq - B) : -(B + sq) / A;  // smaller root
+    }
+    return fminf(fmaxf(t, ta), tb);
 }
 
 template <bool COUNT>
@@ -107,125 +156,120 @@ struct Stats {
 };
 
 // highResolutionTracing over full-resolution texels inside the index box
-// [lo, hi] between t0 and t1. Returns true when a decision was reached.
+// [lo, hi] for u in [u0, u1]. P0, D20: |Ya + u0 V|^2 and (1 - e u0)^2.
+// Returns true when a decision was reached.
 template <int NRMF, bool COUNT>
-__device__ bool fine_walk(const GridDev& g, const Seg& s, size_t pbase, float t0, float t1,
-                          int lo0, int lo1, int hi0, int hi1, float r2a, Decision& out,
-                          Stats<COUNT>& st, bool& step_limited) {
+__device__ bool fine_walk(const GridDev& g, const Seg& s, size_t pbase, float u0, float u1, float P0, float D20,
+                          int lo0, int lo1, int hi0, int hi1, Decision& out, Stats<COUNT>& st, bool& step_limited) {
     const int N = g.N;
-    float L0 = s.c + s.e * t0;
-    int i = texel_of((s.al[0] + s.be[0] * t0) / L0, N, s.dir[0]);
-    int j = texel_of((s.al[1] + s.be[1] * t0) / L0, N, s.dir[1]);
-    i = min(max(i, lo0), hi0);
-    j = min(max(j, lo1), hi1);
-    float tx = s.dir[0] > 0 ? cross_time(s, 0, boundary(s, i + 1, N), t0)
-             : s.dir[0] < 0 ? cross_time(s, 0, boundary(s, i, N), t0) : kInf;
-    float ty = s.dir[1] > 0 ? cross_time(s, 1, boundary(s, j + 1, N), t0)
-             : s.dir[1] < 0 ? cross_time(s, 1, boundary(s, j, N), t0) : kInf;
-    float t = t0;
+    int i = min(max(texel_of(fmaf(s.k[0], u0, s.p0[0]), N, s.dir[0]), lo0), hi0);
+    int j = min(max(texel_of(fmaf(s.k[1], u0, s.p0[1]), N, s.dir[1]), lo1), hi1);
+    float ux = next_cross(s, 0, i, u0), uy = next_cross(s, 1, j, u0);
+    float u = u0, Pa = P0, D2a = D20;
     for (int guard = 0; guard < 4 * N + 8; ++guard) {
-        float tn = fminf(tx, ty);
-        bool last = !(tn < t1);
-        float te = last ? t1 : tn;
-        float r2b = r2_at(s, te);
+        float un = fminf(ux, uy);
+        bool last = !(un < u1);
+        float ue = last ? u1 : un;
+        float Pb = fmaf(fmaf(s.A2, ue, s.A1), ue, s.A0);
+        float Db = fmaf(-s.e, ue, 1.0f);
+        float D2b = Db * Db;
         float d = __ldg(g.dist + pbase + (size_t)j * N + i);
+        float d2 = d * d;
         if (COUNT) st.fine++;
         st.steps++;
         if (g.max_steps > 0 && (int)st.steps >= g.max_steps) { step_limited = true; return true; }
-        if (!(fmaxf(r2a, r2b) < d * d)) {
-            out.i = i;
-            out.j = j;
-            out.ta = t;
-            out.tb = te;
-            out.d = d;
-            float tl = fminf(fmaxf(s.tstar, t), te);
-            float r2lo = r2_at(s, tl);
+        if (!(Pa < d2 * D2a && Pb < d2 * D2b)) {  // the ray reaches the stored distance
+            float ta = tau_of(s, u), tb = tau_of(s, ue);
             float dk = d * g.kappa;
-            if (g.two_way || r2lo <= dk * dk) {
+            out.cls = kUnknown;  // unless the normal test passes below
+            if (g.two_way || r2_tau(s, fminf(fmaxf(s.tstar, ta), tb)) <= dk * dk) {
                 float2 no = NrmTexel<NRMF>::load(g.nrm, pbase + (size_t)j * N + i);
                 float3 n = oct_decode_unnorm(no.x, no.y);
                 if (COUNT) st.normal++;
-                out.cls = (n.x * s.w.x + n.y * s.w.y + n.z * s.w.z) < 0.0f ? kHit : kUnknown;
-            } else {
-                out.cls = kUnknown;  // the ray passes behind the stored surface
-            }
+                if ((n.x * s.w.x + n.y * s.w.y + n.z * s.w.z) < 0.0f) {
+                    float th = hit_time(s, ta, tb, d);
+                    float2 pp = oct_encode(fmaf(th, s.w.x, s.Ya.x), fmaf(th, s.w.y, s.Ya.y), fmaf(th, s.w.z, s.Ya.z));
+                    out.cls = kHit;
+                    out.texel = i + N * j;
+                    out.u = 0.5f * (pp.x + 1.0f);
+                    out.v = 0.5f * (pp.y + 1.0f);
+                }
+            }  // else the ray passes behind the stored surface: UNKNOWN
             return true;
         }
         if (last) return false;
-        if (tx <= ty) {
+        if (ux <= uy) {
             i += s.dir[0];
             if (i < lo0 || i > hi0) return false;
-            tx = cross_time(s, 0, boundary(s, s.dir[0] > 0 ? i + 1 : i, N), te);
+            ux = next_cross(s, 0, i, ue);
         } else {
             j += s.dir[1];
             if (j < lo1 || j > hi1) return false;
-            ty = cross_time(s, 1, boundary(s, s.dir[1] > 0 ? j + 1 : j, N), te);
+            uy = next_cross(s, 1, j, ue);
         }
-        t = te;
-        r2a = r2b;
+        u = ue;
+        Pa = Pb;
+        D2a = D2b;
     }
     return false;
 }
 
 // traceOneRaySegment: low-resolution walk; full-resolution walk in candidates.
-template <int NRMF, bool COUNT>
-__device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, float ta, float tb, bool flat,
-                              Decision& out, Stats<COUNT>& st, bool& step_limited) {
+template <int NRMF, bool COUNT, bool FLAT>
+__device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decision& out, Stats<COUNT>& st,
+                              bool& step_limited) {
     const int N = g.N, M = g.M, k = g.k;
     size_t pbase = (size_t)probe * N * N;
-    float r2a = r2_at(s, ta);
-    if (flat)  // Appendix A RayMarching: the full-resolution map only
-        return fine_walk<NRMF, COUNT>(g, s, pbase, ta, tb, s.lo[0], s.lo[1], s.hi[0], s.hi[1], r2a, out, st,
-                                      step_limited);
+    if (FLAT)  // Appendix A RayMarching: the full-resolution map only
+        return fine_walk<NRMF, COUNT>(g, s, pbase, 0.0f, s.u_end, s.A0, 1.0f, s.lo[0], s.lo[1], s.hi[0], s.hi[1],
+                                      out, st, step_limited);
     const float2* mip = g.mip + (size_t)probe * M * M;
-    float L0 = s.c + s.e * ta;
-    int I = texel_of((s.al[0] + s.be[0] * ta) / L0, N, s.dir[0]) / k;
-    int J = texel_of((s.al[1] + s.be[1] * ta) / L0, N, s.dir[1]) / k;
     int clo0 = s.lo[0] / k, chi0 = s.hi[0] / k, clo1 = s.lo[1] / k, chi1 = s.hi[1] / k;
-    I = min(max(I, clo0), chi0);
-    J = min(max(J, clo1), chi1);
-    float tx = s.dir[0] > 0 ? cross_time(s, 0, boundary(s, (I + 1) * k, N), ta)
-             : s.dir[0] < 0 ? cross_time(s, 0, boundary(s, I * k, N), ta) : kInf;
-    float ty = s.dir[1] > 0 ? cross_time(s, 1, boundary(s, (J + 1) * k, N), ta)
-             : s.dir[1] < 0 ? cross_time(s, 1, boundary(s, J * k, N), ta) : kInf;
-    float t = ta;
+    int I = min(max(texel_of(s.p0[0], N, s.dir[0]) / k, clo0), chi0);
+    int J = min(max(texel_of(s.p0[1], N, s.dir[1]) / k, clo1), chi1);
+    // coarse boundaries are full-resolution boundaries b = I k: same crossings
+    float ux = s.dir[0] == 0 ? kInf : fmaxf(fmaf((float)((s.dir[0] > 0 ? I + 1 : I) * k), s.m[0], s.q[0]), 0.0f);
+    float uy = s.dir[1] == 0 ? kInf : fmaxf(fmaf((float)((s.dir[1] > 0 ? J + 1 : J) * k), s.m[1], s.q[1]), 0.0f);
+    float u = 0.0f, Pa = s.A0, D2a = 1.0f;
+    const float u1 = s.u_end;
     for (int guard = 0; guard < 4 * M + 8; ++guard) {
-        float tn = fminf(tx, ty);
-        bool last = !(tn < tb);
-        float te = last ? tb : tn;
-        float r2b = r2_at(s, te);
+        float un = fminf(ux, uy);
+        bool last = !(un < u1);
+        float ue = last ? u1 : un;
+        float Pb = fmaf(fmaf(s.A2, ue, s.A1), ue, s.A0);
+        float Db = fmaf(-s.e, ue, 1.0f);
+        float D2b = Db * Db;
         float2 mm = __ldg(mip + (size_t)J * M + I);
+        float d2 = mm.x * mm.x;
         if (COUNT) st.coarse++;
         st.steps++;
         if (g.max_steps > 0 && (int)st.steps >= g.max_steps) { step_limited = true; return true; }
-        if (!(fmaxf(r2a, r2b) < mm.x * mm.x)) {  // candidate coarse texel
-            bool behind = false;
+        if (!(Pa < d2 * D2a && Pb < d2 * D2b)) {  // candidate coarse texel
             if (!g.two_way) {
-                float tl = fminf(fmaxf(s.tstar, t), te);
+                float ta = tau_of(s, u), tb = tau_of(s, ue);
                 float dk = mm.y * g.kappa;
-                behind = r2_at(s, tl) > dk * dk;
+                if (r2_tau(s, fminf(fmaxf(s.tstar, ta), tb)) > dk * dk) {
+                    out.cls = kUnknown;  // every full-resolution texel under it is passed behind
+                    return true;
+                }
             }
-            if (behind) {  // every full-resolution texel under it is passed behind
-                out.cls = kUnknown;
-                out.i = out.j = -1;
-                return true;
-            }
-            if (fine_walk<NRMF, COUNT>(g, s, pbase, t, te, I * k, J * k, I * k + k - 1, J * k + k - 1, r2a, out,
+            if (fine_walk<NRMF, COUNT>(g, s, pbase, u, ue, Pa, D2a, I * k, J * k, I * k + k - 1, J * k + k - 1, out,
                                        st, step_limited))
                 return true;
         }
         if (last) return false;
-        if (tx <= ty) {
+        if (ux <= uy) {
             I += s.dir[0];
             if (I < clo0 || I > chi0) return false;
-            tx = cross_time(s, 0, boundary(s, (s.dir[0] > 0 ? I + 1 : I) * k, N), te);
+            ux = fmaxf(fmaf((float)((s.dir[0] > 0 ? I + 1 : I) * k), s.m[0], s.q[0]), ue);
         } else {
             J += s.dir[1];
             if (J < clo1 || J > chi1) return false;
-            ty = cross_time(s, 1, boundary(s, (s.dir[1] > 0 ? J + 1 : J) * k, N), te);
+            uy = fmaxf(fmaf((float)((s.dir[1] > 0 ? J + 1 : J) * k), s.m[1], s.q[1]), ue);
         }
-        t = te;
-        r2a = r2b;
+        u = ue;
+        Pa = Pb;
+        D2a = D2b;
     }
     return false;
 }
@@ -236,65 +280,75 @@ __device__ __forceinline__ float3 probe_pos(const GridDev& g, int p) {
                        grid_plane(g.oz, g.spacing, iz));
 }
 
+// Position and index of corner kq (bit a: +1 along axis a) of cell (c0, c1, c2).
+__device__ __forceinline__ float3 corner_pos(const GridDev& g, int c0, int c1, int c2, int kq) {
+    return make_float3(grid_plane(g.ox, g.spacing, c0 + (kq & 1)), grid_plane(g.oy, g.spacing, c1 + ((kq >> 1) & 1)),
+                       grid_plane(g.oz, g.spacing, c2 + (kq >> 2)));
+}
+__device__ __forceinline__ int corner_index(const GridDev& g, int c0, int c1, int c2, int kq) {
+    return (c0 + (kq & 1)) + g.nx * ((c1 + ((kq >> 1) & 1)) + g.ny * (c2 + (kq >> 2)));
+}
+
+// Cage order (8-probe cage, nearest corner to the entry point P first).
+// Along each axis the squared distance of a corner is one of two values, so
+// d^2(corner) = d^2(nearest) + sum of g_a over the axes where the corner
+// differs from the nearest one, g_a = |dhi_a^2 - dlo_a^2|. With the axes
+// sorted by g (a1 <= a2 <= a3) the order is fixed except for one comparison:
+// n, n^a1, n^a2, {n^a3, n^a1a2}, n^a1a3, n^a2a3, n^a1a2a3.
+// Returns the corner of rank q in bits [3q, 3q + 3).
+__device__ __forceinline__ unsigned cage_order(const GridDev& g, int c0, int c1, int c2, float3 P) {
+    float3 lo = corner_pos(g, c0, c1, c2, 0), hi = corner_pos(g, c0, c1, c2, 7);
+    float dl, dh, ga[3];
+    int n = 0;
+    dl = P.x - lo.x; dh = P.x - hi.x; dl *= dl; dh *= dh; n |= dh < dl ? 1 : 0; ga[0] = fabsf(dh - dl);
+    dl = P.y - lo.y; dh = P.y - hi.y; dl *= dl; dh *= dh; n |= dh < dl ? 2 : 0; ga[1] = fabsf(dh - dl);
+    dl = P.z - lo.z; dh = P.z - hi.z; dl *= dl; dh *= dh; n |= dh < dl ? 4 : 0; ga[2] = fabsf(dh - dl);
+    // sort the three axes by g, ties to the lower axis
+    int a1 = 0, a2 = 1, a3 = 2;
+    float g1 = ga[0], g2 = ga[1], g3 = ga[2];
+    if (g2 < g1) { float t = g1; g1 = g2; g2 = t; int i = a1; a1 = a2; a2 = i; }
+    if (g3 < g2) {
+        float t = g2; g2 = g3; g3 = t; int i = a2; a2 = a3; a3 = i;
+        if (g2 < g1) { t = g1; g1 = g2; g2 = t; i = a1; a1 = a2; a2 = i; }
+    }
+    const unsigned m1 = 1u << a1, m2 = 1u << a2, m3 = 1u << a3, un = (unsigned)n;
+    const bool single_first = g3 < g1 + g2;
+    unsigned r3 = un ^ (single_first ? m3 : (m1 | m2));
+    unsigned r4 = un ^ (single_first ? (m1 | m2) : m3);
+    return un | ((un ^ m1) << 3) | ((un ^ m2) << 6) | (r3 << 9) | (r4 << 12) | ((un ^ (m1 | m3)) << 15) |
+           ((un ^ (m2 | m3)) << 18) | ((un ^ 7u) << 21);
+}
+
 // traceOneProbe over [t0, t1]: split at the probe's axis planes (at most 4
 // single-octant segments, Sec. 4.2); the first non-MISS segment decides.
-template <int NRMF, bool COUNT>
-__device__ void trace_probe(const GridDev& g, const Ray& r, int probe, float t0, float t1, bool flat,
-                            Decision& out, Seg& hit_seg, Stats<COUNT>& st, bool& step_limited) {
-    float3 O = probe_pos(g, probe);
+template <int NRMF, bool COUNT, bool FLAT>
+__device__ void trace_probe(const GridDev& g, const Ray& r, int probe, float3 O, float t0, float t1, Decision& out,
+                            Stats<COUNT>& st, bool& step_limited) {
     float3 Y0 = make_float3(r.X.x - O.x, r.X.y - O.y, r.X.z - O.z);
-    float cut[3];
-    int nc = 0;
-    const float Xa[3] = {r.X.x, r.X.y, r.X.z}, Wa[3] = {r.w.x, r.w.y, r.w.z}, Oa[3] = {O.x, O.y, O.z};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (Wa[a] != 0.0f) {
-            float tc = (Oa[a] - Xa[a]) / Wa[a];
-            if (tc > t0 && tc < t1) cut[nc++] = tc;
-        }
-    }
-    // sort the <= 3 cut points
-    if (nc > 1 && cut[1] < cut[0]) { float x = cut[0]; cut[0] = cut[1]; cut[1] = x; }
-    if (nc > 2 && cut[2] < cut[1]) {
-        float x = cut[1]; cut[1] = cut[2]; cut[2] = x;
-        if (cut[1] < cut[0]) { x = cut[0]; cut[0] = cut[1]; cut[1] = x; }
-    }
+    // cut points strictly inside (t0, t1), sorted: c0 <= c1 <= c2 (inf = none);
+    // the same expression as the cell faces, so a face through the probe is
+    // never a cut
+    float cx = r.w.x != 0.0f ? (O.x - r.X.x) * __frcp_rn(r.w.x) : kInf;
+    float cy = r.w.y != 0.0f ? (O.y - r.X.y) * __frcp_rn(r.w.y) : kInf;
+    float cz = r.w.z != 0.0f ? (O.z - r.X.z) * __frcp_rn(r.w.z) : kInf;
+    cx = (cx > t0 && cx < t1) ? cx : kInf;
+    cy = (cy > t0 && cy < t1) ? cy : kInf;
+    cz = (cz > t0 && cz < t1) ? cz : kInf;
+    float c0 = fminf(cx, fminf(cy, cz)), c2 = fmaxf(cx, fmaxf(cy, cz));
+    float c1 = fmaxf(fminf(cx, cy), fminf(fmaxf(cx, cy), cz));  // median
     out.cls = kMiss;
     float a = t0;
-    for (int sgi = 0; sgi <= nc; ++sgi) {
-        float b = sgi < nc ? cut[sgi] : t1;
+    for (int sgi = 0; sgi < 4; ++sgi) {
+        float b = sgi == 0 ? c0 : (sgi == 1 ? c1 : (sgi == 2 ? c2 : kInf));
+        bool final_seg = !(b < kInf);
+        if (final_seg) b = t1;
         Seg s;
         seg_setup(s, Y0, r.w, a, b, g.N);
-        if (trace_segment<NRMF, COUNT>(g, s, probe, a, b, flat, out, st, step_limited)) {
-            hit_seg = s;
-            return;
-        }
+        if (trace_segment<NRMF, COUNT, FLAT>(g, s, probe, out, st, step_limited)) return;
+        if (final_seg) break;
         a = b;
     }
     out.cls = kMiss;
-}
-
-// Hit point: the first t >= ta with |Y0 + t w| = d, clamped to [ta, tb];
-// when the ray is behind the stored surface at ta it is the smaller root if
-// the ray comes back to d, else the closest approach (ta when receding).
-// |Y0 + t w|^2 = d^2 is A t^2 + 2 B t + C = 0; the roots use the
-// cancellation-free forms.
-__device__ __forceinline__ float hit_time(const Seg& s, float ta, float tb, float d) {
-    float A = s.w.x * s.w.x + s.w.y * s.w.y + s.w.z * s.w.z;
-    float B = s.Y0.x * s.w.x + s.Y0.y * s.w.y + s.Y0.z * s.w.z;
-    float y0 = sqrtf(s.Y0.x * s.Y0.x + s.Y0.y * s.Y0.y + s.Y0.z * s.Y0.z);
-    float C = (y0 - d) * (y0 + d);
-    float sq = sqrtf(fmaxf(B * B - A * C, 0.0f));
-    float t;
-    if (r2_at(s, ta) < d * d) {
-        t = B > 0.0f ? -C / (B + sq) : (sq - B) / A;  // larger root
-    } else {
-        float tstar = -B / A;
-        if (!(tstar > ta)) return ta;
-        if (B * B - A * C < 0.0f) t = tstar;
-        else t = B < 0.0f ? C / (sq - B) : -(B + sq) / A;  // smaller root
-    }
-    return fminf(fmaxf(t, ta), tb);
 }
 
 template <int RADF>
@@ -320,8 +374,8 @@ struct PixelResult {
     float3 rgb;
 };
 
-template <int RADF, int NRMF, bool COUNT>
-__device__ PixelResult trace_ray(const GridDev& g, const Ray& r, bool flat, Stats<COUNT>& st,
+template <int RADF, int NRMF, bool COUNT, bool FLAT>
+__device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& st,
                                  unsigned& cells, unsigned& probes) {
     PixelResult res;
     res.cls = kMiss;
@@ -385,7 +439,8 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, bool flat, Stat
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             tm[a] = step[a] == 0 ? kInf
-                                 : (grid_plane(og[a], g.spacing, c[a] + (step[a] > 0 ? 1 : 0)) - Xa[a]) / Wa[a];
+                                 : (grid_plane(og[a], g.spacing, c[a] + (step[a] > 0 ? 1 : 0)) - Xa[a]) *
+                                       __frcp_rn(Wa[a]);
         int ax = 0;
         if (tm[1] < tm[ax]) ax = 1;
         if (tm[2] < tm[ax]) ax = 2;
@@ -397,49 +452,26 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, bool flat, Stat
         // cage: 8 corner probes, nearest to the entry point first, ties to
         // the lower probe index (corner k has index order k)
         float3 P = make_float3(fmaf(t_in, r.w.x, r.X.x), fmaf(t_in, r.w.y, r.X.y), fmaf(t_in, r.w.z, r.X.z));
-        float dd[8];
-        int ord[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            int p = (c[0] + (q & 1)) + g.nx * ((c[1] + ((q >> 1) & 1)) + g.ny * (c[2] + ((q >> 2) & 1)));
-            float3 O = probe_pos(g, p);
-            float dx = P.x - O.x, dy = P.y - O.y, dz = P.z - O.z;
-            dd[q] = dx * dx + dy * dy + dz * dz;
-            ord[q] = p;
-        }
-#pragma unroll
-        for (int x = 1; x < 8; ++x) {
-#pragma unroll
-            for (int y = x; y > 0; --y) {
-                bool sw = dd[y] < dd[y - 1];
-                float fd = sw ? dd[y - 1] : dd[y];
-                float fe = sw ? dd[y] : dd[y - 1];
-                int oa = sw ? ord[y - 1] : ord[y];
-                int ob = sw ? ord[y] : ord[y - 1];
-                dd[y] = fd; dd[y - 1] = fe;
-                ord[y] = oa; ord[y - 1] = ob;
-            }
-        }
+        const unsigned order = cage_order(g, c[0], c[1], c[2], P);
         int n_unknown = 0;
         for (int q = 0; q < 8; ++q) {
             Decision dec;
-            Seg hs;
             probes++;
-            trace_probe<NRMF, COUNT>(g, r, ord[q], t_in, t_out, flat, dec, hs, st, step_limited);
+            const int kq = (order >> (3 * q)) & 7;
+            const int probe = corner_index(g, c[0], c[1], c[2], kq);
+            trace_probe<NRMF, COUNT, FLAT>(g, r, probe, corner_pos(g, c[0], c[1], c[2], kq), t_in, t_out, dec, st,
+                                           step_limited);
             if (step_limited) {
                 res.cls = kStepLimit;
                 return res;
             }
             if (dec.cls == kHit) {
-                float th = hit_time(hs, dec.ta, dec.tb, dec.d);
-                float yx = fmaf(th, hs.w.x, hs.Y0.x), yy = fmaf(th, hs.w.y, hs.Y0.y), yz = fmaf(th, hs.w.z, hs.Y0.z);
-                float2 pp = oct_encode(yx, yy, yz);
                 res.cls = kHit;
-                res.probe = ord[q];
-                res.u = 0.5f * (pp.x + 1.0f);
-                res.v = 0.5f * (pp.y + 1.0f);
-                res.texel = dec.i + g.N * dec.j;
-                res.rgb = shade<RADF>(g, ord[q], res.u, res.v);
+                res.probe = probe;
+                res.u = dec.u;
+                res.v = dec.v;
+                res.texel = dec.texel;
+                res.rgb = shade<RADF>(g, probe, res.u, res.v);
                 return res;
             }
             if (dec.cls == kMiss) break;

@@ -21,6 +21,7 @@ LFP_TEXEL_F32, LFP_TEXEL_F16 = 0, 1
 LFP_CLASS_MISS, LFP_CLASS_HIT, LFP_CLASS_UNKNOWN, LFP_CLASS_STEPLIMIT = 0, 1, 2, 3
 LFP_MARCH_HIER, LFP_MARCH_FLAT = 0, 1
 LFP_SCHED_AUTO, LFP_SCHED_TILES, LFP_SCHED_PERSISTENT = 0, 1, 2
+LFP_ENGINE_AUTO, LFP_ENGINE_STREAM, LFP_ENGINE_NESTED = 0, 1, 2
 N_COUNTERS = 8
 COUNTER_NAMES = ("coarse", "fine", "normal", "radiance", "cells", "probes", "hits", "rays")
 
@@ -52,7 +53,7 @@ class lfp_outputs(ctypes.Structure):
 
 class lfp_render_opts(ctypes.Structure):
     _fields_ = [("march", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
-                ("schedule", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 class LfpError(RuntimeError):
