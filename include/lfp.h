@@ -216,7 +216,8 @@ lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes);
  * not allowed; a real-time frame loop that must not touch the allocator after
  * start-up; a host whose device memory comes from its own fixed-budget
  * allocator). Same results and outputs as lfp_render_ex with
- * LFP_SCHED_PERSISTENT and 16x8 ray tiles, in one persistent launch for all
+ * LFP_ENGINE_NESTED, LFP_SCHED_PERSISTENT and 16x8 ray tiles, in one
+ * persistent launch for all
  * n_views <= LFP_STATIC_MAX_VIEWS views (more -> LFP_ERR_CAPACITY, nothing
  * is launched). The work-queue head and the view table live in one
  * file-scope device array of 256 B + LFP_STATIC_MAX_VIEWS * 80 B (about

@@ -52,6 +52,7 @@ def test_static_render_matches_persistent_render_twice_in_a_row():
         opts = lfp.lfp_render_opts()
         opts.schedule = lfp.LFP_SCHED_PERSISTENT
         opts.tile_w, opts.tile_h = 16, 8
+        opts.engine = lfp.LFP_ENGINE_NESTED  # the tracer lfp_render_static runs
         lfp.lfp_render_ex(grid.handle, arr, nv, ow, opts, stream)
         got, og = _outputs(lfp, total, dev)
         st = lfp.raw_call("lfp_render_static", grid.handle, arr, nv, ctypes.byref(og), stream)
