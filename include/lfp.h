@@ -175,6 +175,15 @@ lfp_status lfp_render_ex(lfp_grid* grid, const lfp_view* views, int n_views,
                          const lfp_outputs* out, const lfp_render_opts* opts,
                          void* cuda_stream);
 
+/* Autotuner: time every launch configuration (streaming engine; loop-nest
+ * engine with each ray-tile shape, one CTA per tile or persistent) on these
+ * views, keep the fastest as the grid's default for calls that leave the
+ * options zero, and return it in *best (may be NULL). Synchronises the
+ * stream; the outputs (rgb and cls required) are overwritten with the last
+ * run. Do not call it during stream capture. */
+lfp_status lfp_autotune(lfp_grid* grid, const lfp_view* views, int n_views,
+                        const lfp_outputs* out, lfp_render_opts* best, void* cuda_stream);
+
 /* Render into HOST memory: one call that runs lfp_render on device buffers
  * owned by the grid and copies rgb [P][3] f32 and cls [P] u8 back, then
  * synchronises the stream. rgb_host / cls_host: host memory (pinned memory
@@ -194,6 +203,20 @@ lfp_status lfp_render_backward(lfp_grid* grid, const lfp_view* views, int n_view
                                const float* grad_rgb, const uint8_t* cls,
                                const int32_t* aux_probe, const float* aux_uv,
                                float* grad_radiance, void* cuda_stream);
+
+/* lfp_render_backward with a choice of how the scatter-add is reduced:
+ *   LFP_REDUCE_AUTO      the library default (warp-aggregated)
+ *   LFP_REDUCE_ATOMIC    12 f32 atomics per HIT pixel
+ *   LFP_REDUCE_WARP      pixels of a warp that hit the same texel are summed
+ *                        with shuffles first, one atomic per distinct texel
+ *   LFP_REDUCE_SORT      each block sorts its taps by texel in shared memory
+ *                        and issues one atomic per run of equal texels
+ * All give the same sums up to the order of f32 additions. */
+enum { LFP_REDUCE_AUTO = 0, LFP_REDUCE_ATOMIC = 1, LFP_REDUCE_WARP = 2, LFP_REDUCE_SORT = 3 };
+lfp_status lfp_render_backward_ex(lfp_grid* grid, const lfp_view* views, int n_views,
+                                  const float* grad_rgb, const uint8_t* cls,
+                                  const int32_t* aux_probe, const float* aux_uv,
+                                  float* grad_radiance, int reduction, void* cuda_stream);
 
 /* Replace every probe's radiance from a device array [P_total][N][N][3] f32
  * (the fitted parameters); converted to the grid's radiance format. */

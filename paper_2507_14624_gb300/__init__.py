@@ -138,17 +138,54 @@ class ProbeGrid:
         lfp.lfp_render_ex(self.handle, arr, n, o, opts, _stream_handle(stream))
         return out
 
-    def render_backward(self, views, grad_rgb, cls, probe, uv, grad_radiance=None, stream=None):
-        """Adjoint: accumulate into grad_radiance [P][N][N][3] f32 (zeros if None) and return it."""
+    def autotune(self, views, stream=None) -> dict:
+        """Pick the fastest launch configuration for these views (kept as the
+        grid default). Returns it as a dict."""
+        import torch
+        arr, n, total = make_views(views)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
+        cls = torch.empty(total, dtype=torch.uint8, device=dev)
+        o = lfp.lfp_outputs()
+        o.rgb, o.cls = rgb.data_ptr(), cls.data_ptr()
+        b = lfp.lfp_autotune(self.handle, arr, n, o, _stream_handle(stream))
+        return {"engine": b.engine, "tile": (b.tile_w, b.tile_h), "schedule": b.schedule}
+
+    def render_graph(self, views, aux=False, stream=None):
+        """Capture one render of these views in a CUDA graph (outputs are
+        preallocated and reused). Returns (graph, outputs); graph.replay()
+        re-renders into the same tensors."""
+        import torch
+        s = torch.cuda.Stream() if stream is None else stream
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            out = self.render(views, aux=aux, stream=s)  # warm-up outside capture
+        torch.cuda.current_stream().wait_stream(s)
+        arr, n, total = make_views(views)
+        o = lfp.lfp_outputs()
+        o.rgb, o.cls = out["rgb"].data_ptr(), out["cls"].data_ptr()
+        o.aux_probe = out["probe"].data_ptr() if aux else None
+        o.aux_uv = out["uv"].data_ptr() if aux else None
+        graph = torch.cuda.CUDAGraph()
+        keep = (arr, o)
+        with torch.cuda.graph(graph, stream=s):
+            lfp.lfp_render_ex(self.handle, arr, n, o, None, _stream_handle(s))
+        graph._lfp_keep = keep
+        return graph, out
+
+    def render_backward(self, views, grad_rgb, cls, probe, uv, grad_radiance=None, reduction=0, stream=None):
+        """Adjoint: accumulate into grad_radiance [P][N][N][3] f32 (zeros if None) and return it.
+        reduction: lfp.LFP_REDUCE_* (atomics, warp-aggregated, sort by texel)."""
         import torch
         arr, n, total = make_views(views)
         if grad_radiance is None:
             grad_radiance = torch.zeros((self.n_probes, self.N, self.N, 3), dtype=torch.float32,
                                         device=grad_rgb.device)
         g = grad_rgb.contiguous()
-        lfp.lfp_render_backward(self.handle, arr, n, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(cls.data_ptr()),
-                                ctypes.c_void_p(probe.data_ptr()), ctypes.c_void_p(uv.data_ptr()),
-                                ctypes.c_void_p(grad_radiance.data_ptr()), _stream_handle(stream))
+        lfp.lfp_render_backward_ex(self.handle, arr, n, ctypes.c_void_p(g.data_ptr()),
+                                   ctypes.c_void_p(cls.data_ptr()), ctypes.c_void_p(probe.data_ptr()),
+                                   ctypes.c_void_p(uv.data_ptr()), ctypes.c_void_p(grad_radiance.data_ptr()),
+                                   reduction, _stream_handle(stream))
         return grad_radiance
 
     def render_to_host(self, views, rgb_host, cls_host, stream=None):

@@ -35,6 +35,7 @@ struct lfp_grid {
     std::vector<unsigned char> uploaded;
     int tile_w = 16, tile_h = 8;        // default ray tile (nested engine)
     int stream_blocks = 0;              // persistent grid of the stream engine (0 = not sized yet)
+    int engine = LFP_ENGINE_STREAM;     // default engine (set by lfp_autotune)
     int schedule = LFP_SCHED_TILES;
 };
 
@@ -168,7 +169,7 @@ bool valid_tile(int w, int h) {
 
 lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const OutDev& out,
                        const lfp_render_opts* opts, cudaStream_t s) {
-    int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0, engine = LFP_ENGINE_STREAM;
+    int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0, engine = g->engine;
     if (opts) {
         if (opts->engine < LFP_ENGINE_AUTO || opts->engine > LFP_ENGINE_NESTED) return LFP_ERR_INVALID_ARG;
         if (opts->engine != LFP_ENGINE_AUTO) engine = opts->engine;
@@ -407,6 +408,73 @@ lfp_status lfp_render(lfp_grid* g, const lfp_view* views, int n_views, float* rg
     return lfp_render_ex(g, views, n_views, &o, nullptr, stream);
 }
 
+lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const lfp_outputs* o,
+                        lfp_render_opts* best, void* stream) {
+    if (!g || !o || !o->rgb || !o->cls) return LFP_ERR_INVALID_ARG;
+    LFP_TRY(check_views(views, n_views));
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    OutDev out;
+    out.rgb = o->rgb;
+    out.cls = o->cls;
+    out.aux_probe = o->aux_probe;
+    out.aux_uv = o->aux_uv;
+    out.hit_texel = nullptr;
+    out.counters = nullptr;
+    std::vector<lfp_render_opts> cand;
+    lfp_render_opts c;
+    std::memset(&c, 0, sizeof(c));
+    c.engine = LFP_ENGINE_STREAM;
+    cand.push_back(c);
+    const int shapes[5][2] = {{8, 4}, {8, 8}, {16, 8}, {16, 16}, {32, 8}};
+    for (auto& sh : shapes)
+        for (int sched : {LFP_SCHED_TILES, LFP_SCHED_PERSISTENT}) {
+            std::memset(&c, 0, sizeof(c));
+            c.engine = LFP_ENGINE_NESTED;
+            c.tile_w = sh[0];
+            c.tile_h = sh[1];
+            c.schedule = sched;
+            cand.push_back(c);
+        }
+    cudaEvent_t e0, e1;
+    LFP_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return LFP_ERR_CUDA;
+    }
+    lfp_status st = LFP_OK;
+    float best_ms = 3.4e38f;
+    lfp_render_opts pick = cand[0];
+    for (const lfp_render_opts& k : cand) {
+        for (int w = 0; w < 2 && st == LFP_OK; ++w) st = render_impl(g, views, n_views, out, &k, s);
+        if (st != LFP_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = LFP_ERR_CUDA; break; }
+        for (int r = 0; r < 3 && st == LFP_OK; ++r) st = render_impl(g, views, n_views, out, &k, s);
+        float ms = 0.f;
+        if (st != LFP_OK || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            if (st == LFP_OK) st = LFP_ERR_CUDA;
+            break;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            pick = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LFP_OK) return st;
+    g->engine = pick.engine;
+    if (pick.engine == LFP_ENGINE_NESTED) {
+        g->tile_w = pick.tile_w;
+        g->tile_h = pick.tile_h;
+        g->schedule = pick.schedule;
+    }
+    if (best) *best = pick;
+    return LFP_OK;
+}
+
 lfp_status lfp_render_to_host(lfp_grid* g, const lfp_view* views, int n_views, float* rgb_host, uint8_t* cls_host,
                               void* stream) {
     if (!g) return LFP_ERR_INVALID_ARG;
@@ -442,7 +510,18 @@ lfp_status lfp_render_to_host(lfp_grid* g, const lfp_view* views, int n_views, f
 lfp_status lfp_render_backward(lfp_grid* g, const lfp_view* views, int n_views, const float* grad_rgb,
                                const uint8_t* cls, const int32_t* aux_probe, const float* aux_uv,
                                float* grad_radiance, void* stream) {
+    return lfp_render_backward_ex(g, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance,
+                                  LFP_REDUCE_AUTO, stream);
+}
+
+lfp_status lfp_render_backward_ex(lfp_grid* g, const lfp_view* views, int n_views, const float* grad_rgb,
+                                  const uint8_t* cls, const int32_t* aux_probe, const float* aux_uv,
+                                  float* grad_radiance, int reduction, void* stream) {
     if (!g || !grad_rgb || !cls || !aux_probe || !aux_uv || !grad_radiance) return LFP_ERR_INVALID_ARG;
+    if (reduction < LFP_REDUCE_AUTO || reduction > LFP_REDUCE_SORT) return LFP_ERR_INVALID_ARG;
+    // warp aggregation: fastest measured (maps are magnified, so many pixels
+    // of a warp share texels)
+    if (reduction == LFP_REDUCE_AUTO) reduction = LFP_REDUCE_WARP;
     LFP_TRY(check_views(views, n_views));
     DeviceGuard dg(g->device);
     if (!dg.ok) return LFP_ERR_CUDA;
@@ -456,7 +535,8 @@ lfp_status lfp_render_backward(lfp_grid* g, const lfp_view* views, int n_views, 
             pb.out_offset[i] = v.out_offset;
             pb.begin[i + 1] = pb.begin[i] + (long long)v.W * v.H;
         }
-        LFP_CUDA(launch_backward(g->desc.N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, (cudaStream_t)stream));
+        LFP_CUDA(launch_backward(g->desc.N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, reduction,
+                                 (cudaStream_t)stream));
     }
     return LFP_OK;
 }

@@ -28,9 +28,11 @@ cudaError_t launch_encode_normals(const float* xyz, void* nrm, int nrm_fmt, long
 cudaError_t launch_convert_radiance(const float* rgb, void* rad, int rad_fmt, long long n, cudaStream_t s);
 // per-block min/max of the distance maps for `count` probes
 cudaError_t launch_build_mip(const float* dist, float2* mip, int count, int N, int M, cudaStream_t s);
-// adjoint scatter into grad_radiance [P][N][N][3]
+// adjoint scatter into grad_radiance [P][N][N][3]; reduction: 1 per-pixel
+// atomics, 2 warp-aggregated atomics, 3 block-local sort by texel
 cudaError_t launch_backward(int N, const PixBatch& pb, const float* grad_rgb, const uint8_t* cls,
-                            const int32_t* aux_probe, const float* aux_uv, float* grad_rad, cudaStream_t s);
+                            const int32_t* aux_probe, const float* aux_uv, float* grad_rad, int reduction,
+                            cudaStream_t s);
 
 // Read-only access to a grid for render entry points outside api.cu.
 struct GridAccess {

@@ -1,6 +1,8 @@
 // Upload-time conversions, the min/max low-resolution map and the adjoint.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "lfp_device.cuh"
 #include "lfp_internal.h"
 
@@ -93,6 +95,163 @@ __global__ void backward_kernel(int N, PixBatch pb, const float* __restrict__ gr
     }
 }
 
+// Warp-aggregated adjoint: pixels of one warp that hit the same texel (the
+// maps are magnified: hundreds of pixels per texel at 1080p) are summed with
+// shuffles and written by one atomic per distinct texel and channel.
+__global__ void backward_warp_kernel(int N, PixBatch pb, const float* __restrict__ grad_rgb,
+                                     const uint8_t* __restrict__ cls, const int32_t* __restrict__ aux_probe,
+                                     const float* __restrict__ aux_uv, float* __restrict__ grad_rad) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long total = pb.begin[pb.n];
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const size_t NN = (size_t)N * N;
+    for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < total;
+         base += warps * 32) {
+        long long q = base + lane;
+        bool hit = false;
+        long long o = 0;
+        int p = -1;
+        if (q < total) {
+            int lo = 0, hi = pb.n - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (pb.begin[mid] <= q) lo = mid; else hi = mid - 1;
+            }
+            o = pb.out_offset[lo] + (q - pb.begin[lo]);
+            p = aux_probe[o];
+            hit = cls[o] == kHit && p >= 0;
+        }
+        int idx[4];
+        float w[4] = {0.f, 0.f, 0.f, 0.f};
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        if (hit) {
+            bilinear_taps(N, aux_uv[2 * o], aux_uv[2 * o + 1], idx, w);
+            g0 = grad_rgb[3 * o];
+            g1 = grad_rgb[3 * o + 1];
+            g2 = grad_rgb[3 * o + 2];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            unsigned long long key = hit ? (unsigned long long)p * NN + (unsigned long long)idx[k] : ~0ull;
+            float vx = w[k] * g0, vy = w[k] * g1, vz = w[k] * g2;
+            unsigned todo = __ballot_sync(full, hit);
+            while (todo) {
+                int src = __ffs(todo) - 1;
+                unsigned long long kk = __shfl_sync(full, key, src);
+                bool mine = hit && key == kk;
+                unsigned grp = __ballot_sync(full, mine);
+                float sx = mine ? vx : 0.f, sy = mine ? vy : 0.f, sz = mine ? vz : 0.f;
+                if (__popc(grp) > 1) {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        sx += __shfl_xor_sync(full, sx, off);
+                        sy += __shfl_xor_sync(full, sy, off);
+                        sz += __shfl_xor_sync(full, sz, off);
+                    }
+                }
+                if (lane == src) {
+                    float* t = grad_rad + 3 * kk;
+                    atomicAdd(t + 0, sx);
+                    atomicAdd(t + 1, sy);
+                    atomicAdd(t + 2, sz);
+                }
+                todo &= ~grp;
+            }
+        }
+    }
+}
+
+// Sort-by-texel adjoint: each block sorts its pixels' 4 x blockDim taps by
+// texel (bitonic sort in shared memory), sums runs of equal texels and
+// issues one atomic per run and channel.
+constexpr int kSortThreads = 256;
+constexpr int kSortTaps = 4 * kSortThreads;
+
+__global__ void __launch_bounds__(kSortThreads) backward_sort_kernel(int N, PixBatch pb,
+                                                                     const float* __restrict__ grad_rgb,
+                                                                     const uint8_t* __restrict__ cls,
+                                                                     const int32_t* __restrict__ aux_probe,
+                                                                     const float* __restrict__ aux_uv,
+                                                                     float* __restrict__ grad_rad) {
+    __shared__ unsigned long long s_key[kSortTaps];
+    __shared__ float s_v[kSortTaps][3];
+    __shared__ unsigned short s_src[kSortTaps];
+    const long long total = pb.begin[pb.n];
+    const size_t NN = (size_t)N * N;
+    for (long long base = (long long)blockIdx.x * kSortThreads; base < total; base += (long long)gridDim.x * kSortThreads) {
+        long long q = base + threadIdx.x;
+        bool hit = false;
+        long long o = 0;
+        int p = -1;
+        if (q < total) {
+            int lo = 0, hi = pb.n - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (pb.begin[mid] <= q) lo = mid; else hi = mid - 1;
+            }
+            o = pb.out_offset[lo] + (q - pb.begin[lo]);
+            p = aux_probe[o];
+            hit = cls[o] == kHit && p >= 0;
+        }
+        int idx[4];
+        float w[4] = {0.f, 0.f, 0.f, 0.f};
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        if (hit) {
+            bilinear_taps(N, aux_uv[2 * o], aux_uv[2 * o + 1], idx, w);
+            g0 = grad_rgb[3 * o];
+            g1 = grad_rgb[3 * o + 1];
+            g2 = grad_rgb[3 * o + 2];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int e = 4 * threadIdx.x + k;
+            s_key[e] = hit ? (unsigned long long)p * NN + (unsigned long long)idx[k] : ~0ull;
+            s_v[e][0] = w[k] * g0;
+            s_v[e][1] = w[k] * g1;
+            s_v[e][2] = w[k] * g2;
+            s_src[e] = (unsigned short)e;
+        }
+        __syncthreads();
+        // bitonic sort of (key, src) pairs; values follow through src
+        for (int size = 2; size <= kSortTaps; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = threadIdx.x; t < kSortTaps / 2; t += kSortThreads) {
+                    int a = 2 * t - (t & (stride - 1));
+                    int b = a + stride;
+                    bool up = (a & size) == 0;
+                    unsigned long long ka = s_key[a], kb = s_key[b];
+                    if ((ka > kb) == up) {
+                        s_key[a] = kb;
+                        s_key[b] = ka;
+                        unsigned short x = s_src[a];
+                        s_src[a] = s_src[b];
+                        s_src[b] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // run heads sum their run and write it
+        for (int e = threadIdx.x; e < kSortTaps; e += kSortThreads) {
+            unsigned long long k = s_key[e];
+            if (k == ~0ull || (e > 0 && s_key[e - 1] == k)) continue;
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+            for (int f = e; f < kSortTaps && s_key[f] == k; ++f) {
+                int src = s_src[f];
+                sx += s_v[src][0];
+                sy += s_v[src][1];
+                sz += s_v[src][2];
+            }
+            float* t = grad_rad + 3 * k;
+            atomicAdd(t + 0, sx);
+            atomicAdd(t + 1, sy);
+            atomicAdd(t + 2, sz);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_encode_normals(const float* xyz, void* nrm, int nrm_fmt, long long n, cudaStream_t s) {
@@ -114,10 +273,17 @@ cudaError_t launch_build_mip(const float* dist, float2* mip, int count, int N, i
 }
 
 cudaError_t launch_backward(int N, const PixBatch& pb, const float* grad_rgb, const uint8_t* cls,
-                            const int32_t* aux_probe, const float* aux_uv, float* grad_rad, cudaStream_t s) {
+                            const int32_t* aux_probe, const float* aux_uv, float* grad_rad, int reduction,
+                            cudaStream_t s) {
     long long total = pb.begin[pb.n];
     if (total == 0) return cudaSuccess;
-    backward_kernel<<<blocks_for(total), kThreads, 0, s>>>(N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
+    if (reduction == 2)
+        backward_warp_kernel<<<blocks_for(total), kThreads, 0, s>>>(N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
+    else if (reduction == 3)
+        backward_sort_kernel<<<(int)std::min<long long>((total + kSortThreads - 1) / kSortThreads, 1 << 20),
+                               kSortThreads, 0, s>>>(N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
+    else
+        backward_kernel<<<blocks_for(total), kThreads, 0, s>>>(N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
     return cudaGetLastError();
 }
 

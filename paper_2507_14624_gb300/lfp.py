@@ -22,6 +22,7 @@ LFP_CLASS_MISS, LFP_CLASS_HIT, LFP_CLASS_UNKNOWN, LFP_CLASS_STEPLIMIT = 0, 1, 2,
 LFP_MARCH_HIER, LFP_MARCH_FLAT = 0, 1
 LFP_SCHED_AUTO, LFP_SCHED_TILES, LFP_SCHED_PERSISTENT = 0, 1, 2
 LFP_ENGINE_AUTO, LFP_ENGINE_STREAM, LFP_ENGINE_NESTED = 0, 1, 2
+LFP_REDUCE_AUTO, LFP_REDUCE_ATOMIC, LFP_REDUCE_WARP, LFP_REDUCE_SORT = 0, 1, 2, 3
 N_COUNTERS = 8
 COUNTER_NAMES = ("coarse", "fine", "normal", "radiance", "cells", "probes", "hits", "rays")
 
@@ -74,7 +75,9 @@ def _load():
         "lfp_render_ex": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
         "lfp_render_to_host": ([vp, P(lfp_view), i, vp, vp, vp], i),
         "lfp_render_static": ([vp, P(lfp_view), i, P(lfp_outputs), vp], i),
+        "lfp_autotune": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
         "lfp_render_backward": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, vp], i),
+        "lfp_render_backward_ex": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, i, vp], i),
         "lfp_set_radiance": ([vp, vp, vp], i),
         "lfp_check_flags": ([vp, vp], i),
         "lfp_grid_bytes": ([P(lfp_grid_desc), P(ctypes.c_ulonglong)], i),
@@ -129,6 +132,13 @@ def lfp_render_static(grid, views, n_views, outputs: lfp_outputs, stream) -> Non
     _check(_lib.lfp_render_static(grid, views, n_views, ctypes.byref(outputs), stream), "lfp_render_static")
 
 
+def lfp_autotune(grid, views, n_views, outputs: lfp_outputs, stream) -> lfp_render_opts:
+    """Time the launch configurations, keep the fastest as the grid default, return it."""
+    best = lfp_render_opts()
+    _check(_lib.lfp_autotune(grid, views, n_views, ctypes.byref(outputs), ctypes.byref(best), stream), "lfp_autotune")
+    return best
+
+
 def lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream) -> None:
     _check(_lib.lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream), "lfp_render_to_host")
 
@@ -136,6 +146,12 @@ def lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream) -> None
 def lfp_render_backward(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, stream) -> None:
     _check(_lib.lfp_render_backward(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, stream),
            "lfp_render_backward")
+
+
+def lfp_render_backward_ex(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, reduction,
+                           stream) -> None:
+    _check(_lib.lfp_render_backward_ex(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance,
+                                       reduction, stream), "lfp_render_backward_ex")
 
 
 def lfp_set_radiance(grid, dev_radiance, stream) -> None:

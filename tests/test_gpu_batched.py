@@ -1,0 +1,66 @@
+"""Batching: many views in one launch, CUDA-graph capture and the autotuner."""
+import pytest
+
+import synth
+from conftest import load_workload
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _grid(name):
+    import paper_2507_14624_gb300 as lfpk
+    sc, views, d, n, r = load_workload(name)
+    g = lfpk.ProbeGrid(sc.grid)
+    g.upload(d, n, r)
+    return lfpk, sc, views, g
+
+
+def _mixed_views(sc, k=7):
+    sizes = [(160, 120), (64, 48), (97, 61), (200, 90), (32, 32), (150, 150), (1, 7)]
+    return [synth.random_view(sc, 800 + i, *sizes[i % len(sizes)], 60.0 + 5 * i) for i in range(k)]
+
+
+def test_graph_replay_equals_direct_render():
+    lfpk, sc, views, g = _grid("tiny")
+    vs = _mixed_views(sc)
+    direct = g.render(vs, aux=True)
+    graph, out = g.render_graph(vs, aux=True)
+    for t in out.values():
+        t.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for k in ("rgb", "cls", "probe", "uv"):
+        assert torch.equal(out[k], direct[k]), k
+    graph.replay()  # a second replay rewrites the same outputs
+    torch.cuda.synchronize()
+    assert torch.equal(out["cls"], direct["cls"])
+
+
+def test_autotune_keeps_results_and_sets_a_default():
+    lfpk, sc, views, g = _grid("tiny")
+    vs = _mixed_views(sc, 4)
+    before = g.render(vs, hit_texel=True)
+    best = g.autotune(vs)
+    assert best["engine"] in (lfpk.LFP_ENGINE_STREAM, lfpk.LFP_ENGINE_NESTED)
+    if best["engine"] == lfpk.LFP_ENGINE_NESTED:
+        assert best["tile"] in ((8, 4), (8, 8), (16, 8), (16, 16), (32, 8))
+    after = g.render(vs, hit_texel=True)  # default options now follow the tuned config
+    for k in ("cls", "probe", "texel"):
+        assert torch.equal(before[k], after[k]), k
+    assert (before["rgb"] - after["rgb"]).abs().max().item() <= 1e-4
+
+
+def test_more_than_128_views_span_several_launches():
+    """Views travel as kernel parameters, 128 per launch: a 300-view batch is
+    split and must equal per-view renders."""
+    lfpk, sc, views, g = _grid("tiny")
+    vs = [synth.random_view(sc, 2000 + i, 9 + i % 5, 7 + i % 3, 60.0) for i in range(300)]
+    batch = g.render(vs, hit_texel=True)
+    off = 0
+    for i, v in enumerate(vs):
+        if i % 37 == 0:
+            single = g.render([v], hit_texel=True)
+            for k in ("cls", "texel"):
+                assert torch.equal(batch[k][off:off + v.n_pixels], single[k]), (i, k)
+        off += v.n_pixels
