@@ -80,3 +80,17 @@ def test_autograd_function_and_a_short_fit():
         opt.step()
         first = loss.item() if first is None else first
     assert loss.item() < 0.05 * first
+
+
+def test_fit_reaches_the_noise_floor():
+    """Targets = render + N(0, sigma^2); radiance re-initialised U[0,1] and
+    fitted with Adam through the adjoint: the per-channel MSE on the target
+    views falls to the noise floor sigma^2 (the loss is quadratic in radiance)."""
+    from paper_2507_14624_gb300 import fit
+    lfpk, g, sc, v, d, n, r, grid = _setup(N=32, M=8, W=64, H=64)
+    views = [v] + [synth.random_view(sc, 1200 + k, 64, 64, 60.0) for k in range(7)]
+    sigma = 0.01
+    targets = fit.make_targets(grid, views, sigma=sigma, seed=404)
+    rad, hist = fit.fit_radiance(grid, views, targets, steps=300, lr=2e-2, seed=404)
+    mse = hist[-1][1]
+    assert 0.5 * sigma ** 2 <= mse <= 2.0 * sigma ** 2, hist[-1]
