@@ -23,16 +23,16 @@ namespace {
 using namespace trace;
 
 #ifndef LFP_STREAM_WALK_STEPS
-#define LFP_STREAM_WALK_STEPS 16
+#define LFP_STREAM_WALK_STEPS 64
 #endif
 #ifndef LFP_STREAM_BATCH_PCT
 #define LFP_STREAM_BATCH_PCT 75
 #endif
 #ifndef LFP_STREAM_MIN_BLOCKS
-#define LFP_STREAM_MIN_BLOCKS 5
+#define LFP_STREAM_MIN_BLOCKS 8
 #endif
 constexpr int kStreamThreads = 128;
-constexpr int kWalkSteps = LFP_STREAM_WALK_STEPS;  // texel visits per lane between control rounds
+constexpr int kWalkSteps = LFP_STREAM_WALK_STEPS;  // most texel visits per lane between control rounds
 constexpr int kBatchPct = LFP_STREAM_BATCH_PCT;     // transitions run once this % of busy lanes wait
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -49,19 +49,14 @@ enum Mode : int {
     kExit          // no rays left
 };
 
-// Per-lane state, kept in registers (no member is indexed at run time).
+// Per-lane state. The walk's working set lives in registers (Lane); the
+// fields only the control round touches live in shared memory, one slot per
+// thread in structure-of-arrays layout (conflict-free), which frees registers
+// for more resident warps.
 struct Lane {
     int mode;
-    float3 X, w;         // the ray
-    long long o;         // output index
-    int c0, c1, c2;      // current cell
-    int cbits;           // step signs (2 bits per axis: 1 +, 2 -), bits 6-7 exit axis,
-                         // bit 8 last cell, bit 9 saw UNKNOWN
-    float t_in, t_out;
-    unsigned order;      // cage order: corner of rank q in bits [3q, 3q + 3)
-    int q, kq, probe;    // rank, corner bits and index of the current probe
-    float cut0, cut1, cut2, seg_a, seg_b;
-    int segi, seg_final;
+    float3 w;            // ray direction
+    int probe;           // current probe
     // segment (see Seg): u-parametrised octant line
     float3 Ya;
     float cp, e, m0, m1, q0, q1, p00, p01, k0, k1, A0, A1, A2, u_end, tstar;
@@ -74,8 +69,20 @@ struct Lane {
     float ux, uy, u, u1, Pa, D2a;  // after a HIT: (ux, uy) hold the shading uv
     int I, J, lastc;
     float uxc, uyc, uec;
-    int cls;
 };
+
+// control-round fields in shared memory
+enum ColdF { kX0, kX1, kX2, kTin, kTout, kCut0, kCut1, kCut2, kSegA, kSegB, kNumColdF };
+enum ColdI { kC0, kC1, kC2, kCbits, kOrder, kQ, kKq, kSegI, kSegFinal, kCls, kNumColdI };
+// kCbits: step signs (2 bits per axis: 1 +, 2 -), bits 6-7 exit axis, bit 8
+// last cell, bit 9 saw UNKNOWN. kOrder: corner of rank q in bits [3q, 3q + 3).
+__shared__ float sh_f[kNumColdF][kStreamThreads];
+__shared__ int sh_i[kNumColdI][kStreamThreads];
+__shared__ long long sh_o[kStreamThreads];  // output index of the lane's ray
+
+__device__ __forceinline__ float& CF(int f) { return sh_f[f][threadIdx.x]; }
+__device__ __forceinline__ int& CI(int f) { return sh_i[f][threadIdx.x]; }
+__device__ __forceinline__ float3 ray_X() { return make_float3(CF(kX0), CF(kX1), CF(kX2)); }
 
 __device__ __forceinline__ int step_of(int bits, int a) {
     int v = (bits >> (2 * a)) & 3;
@@ -83,10 +90,10 @@ __device__ __forceinline__ int step_of(int bits, int a) {
 }
 
 // Grid-iterator set-up for a new ray; returns false if it misses the grid.
-__device__ __forceinline__ bool ray_enter_grid(const GridDev& g, Lane& L) {
+__device__ __forceinline__ bool ray_enter_grid(const GridDev& g, float3 X, float3 w) {
     const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
     const float og[3] = {g.ox, g.oy, g.oz};
-    const float Xa[3] = {L.X.x, L.X.y, L.X.z}, Wa[3] = {L.w.x, L.w.y, L.w.z};
+    const float Xa[3] = {X.x, X.y, X.z}, Wa[3] = {w.x, w.y, w.z};
     float t_enter = 0.0f, t_exit = kInf;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -108,60 +115,66 @@ __device__ __forceinline__ bool ray_enter_grid(const GridDev& g, Lane& L) {
         c[a] = min(max((int)floorf((p - og[a]) / g.spacing), 0), nc[a] - 1);
         bits |= (Wa[a] > 0.0f ? 1 : (Wa[a] < 0.0f ? 2 : 0)) << (2 * a);
     }
-    L.c0 = c[0];
-    L.c1 = c[1];
-    L.c2 = c[2];
-    L.cbits = bits;
-    L.t_in = 0.0f;
+    CI(kC0) = c[0];
+    CI(kC1) = c[1];
+    CI(kC2) = c[2];
+    CI(kCbits) = bits;
+    CF(kTin) = 0.0f;
     return true;
 }
 
 // Cell c: its exit (3D DDA) and its cage order, nearest corner to the entry first.
-__device__ __forceinline__ void cell_start(const GridDev& g, Lane& L) {
+__device__ __forceinline__ void cell_start(const GridDev& g, const Lane& L) {
     const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
     const float og[3] = {g.ox, g.oy, g.oz};
-    const float Xa[3] = {L.X.x, L.X.y, L.X.z}, Wa[3] = {L.w.x, L.w.y, L.w.z};
-    const int c[3] = {L.c0, L.c1, L.c2};
+    const float3 X = ray_X();
+    const float Xa[3] = {X.x, X.y, X.z}, Wa[3] = {L.w.x, L.w.y, L.w.z};
+    const int c[3] = {CI(kC0), CI(kC1), CI(kC2)};
+    const int cbits = CI(kCbits);
     float tm[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        int st = step_of(L.cbits, a);
+        int st = step_of(cbits, a);
         tm[a] = st == 0 ? kInf
                         : (grid_plane(og[a], g.spacing, c[a] + (st > 0 ? 1 : 0)) - Xa[a]) * __frcp_rn(Wa[a]);
     }
     int ax = 0;
     if (tm[1] < tm[ax]) ax = 1;
     if (tm[2] < tm[ax]) ax = 2;
-    int st = step_of(L.cbits, ax);
+    int st = step_of(cbits, ax);
     int cax = ax == 0 ? c[0] : (ax == 1 ? c[1] : c[2]);
     int ncax = ax == 0 ? nc[0] : (ax == 1 ? nc[1] : nc[2]);
     int nxt = cax + st;
     bool last = st == 0 || nxt < 0 || nxt > ncax - 1;
     float tax = ax == 0 ? tm[0] : (ax == 1 ? tm[1] : tm[2]);
-    L.cbits = (L.cbits & 0x23f) | (ax << 6) | (last ? 0x100 : 0);
-    L.t_out = last ? kInf : tax;
-    float3 P = make_float3(fmaf(L.t_in, L.w.x, L.X.x), fmaf(L.t_in, L.w.y, L.X.y), fmaf(L.t_in, L.w.z, L.X.z));
-    L.order = cage_order(g, L.c0, L.c1, L.c2, P);
-    L.q = 0;
+    CI(kCbits) = (cbits & 0x23f) | (ax << 6) | (last ? 0x100 : 0);
+    CF(kTout) = last ? kInf : tax;
+    const float t_in = CF(kTin);
+    float3 P = make_float3(fmaf(t_in, L.w.x, X.x), fmaf(t_in, L.w.y, X.y), fmaf(t_in, L.w.z, X.z));
+    CI(kOrder) = (int)cage_order(g, c[0], c[1], c[2], P);
+    CI(kQ) = 0;
 }
 
 // Probe of rank q: its index and the cut points of the octant split.
 __device__ __forceinline__ void probe_start(const GridDev& g, Lane& L) {
-    L.kq = (L.order >> (3 * L.q)) & 7;
-    L.probe = corner_index(g, L.c0, L.c1, L.c2, L.kq);
-    float3 O = corner_pos(g, L.c0, L.c1, L.c2, L.kq);
-    const float t0 = L.t_in, t1 = L.t_out;
-    float cx = L.w.x != 0.0f ? (O.x - L.X.x) * __frcp_rn(L.w.x) : kInf;
-    float cy = L.w.y != 0.0f ? (O.y - L.X.y) * __frcp_rn(L.w.y) : kInf;
-    float cz = L.w.z != 0.0f ? (O.z - L.X.z) * __frcp_rn(L.w.z) : kInf;
+    const int kq = ((unsigned)CI(kOrder) >> (3 * CI(kQ))) & 7;
+    const int c0 = CI(kC0), c1 = CI(kC1), c2 = CI(kC2);
+    CI(kKq) = kq;
+    L.probe = corner_index(g, c0, c1, c2, kq);
+    float3 O = corner_pos(g, c0, c1, c2, kq);
+    const float3 X = ray_X();
+    const float t0 = CF(kTin), t1 = CF(kTout);
+    float cx = L.w.x != 0.0f ? (O.x - X.x) * __frcp_rn(L.w.x) : kInf;
+    float cy = L.w.y != 0.0f ? (O.y - X.y) * __frcp_rn(L.w.y) : kInf;
+    float cz = L.w.z != 0.0f ? (O.z - X.z) * __frcp_rn(L.w.z) : kInf;
     cx = (cx > t0 && cx < t1) ? cx : kInf;
     cy = (cy > t0 && cy < t1) ? cy : kInf;
     cz = (cz > t0 && cz < t1) ? cz : kInf;
-    L.cut0 = fminf(cx, fminf(cy, cz));
-    L.cut2 = fmaxf(cx, fmaxf(cy, cz));
-    L.cut1 = fmaxf(fminf(cx, cy), fminf(fmaxf(cx, cy), cz));
-    L.segi = 0;
-    L.seg_a = t0;
+    CF(kCut0) = fminf(cx, fminf(cy, cz));
+    CF(kCut2) = fmaxf(cx, fmaxf(cy, cz));
+    CF(kCut1) = fmaxf(fminf(cx, cy), fminf(fmaxf(cx, cy), cz));
+    CI(kSegI) = 0;
+    CF(kSegA) = t0;
 }
 
 // Low-resolution index box of the segment's quadrant.
@@ -176,13 +189,16 @@ __device__ __forceinline__ void coarse_box(const GridDev& g, Lane& L) {
 // Segment segi: the octant line (same arithmetic as seg_setup) and the
 // start of the low-resolution walk.
 __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
-    float b = L.segi == 0 ? L.cut0 : (L.segi == 1 ? L.cut1 : (L.segi == 2 ? L.cut2 : kInf));
-    L.seg_final = !(b < kInf);
-    if (L.seg_final) b = L.t_out;
-    L.seg_b = b;
-    float3 O = corner_pos(g, L.c0, L.c1, L.c2, L.kq);
+    const int segi = CI(kSegI);
+    float b = segi == 0 ? CF(kCut0) : (segi == 1 ? CF(kCut1) : (segi == 2 ? CF(kCut2) : kInf));
+    const bool final_seg = !(b < kInf);
+    CI(kSegFinal) = final_seg;
+    if (final_seg) b = CF(kTout);
+    CF(kSegB) = b;
+    float3 O = corner_pos(g, CI(kC0), CI(kC1), CI(kC2), CI(kKq));
+    const float3 X = ray_X();
     Seg s;
-    seg_setup(s, make_float3(L.X.x - O.x, L.X.y - O.y, L.X.z - O.z), L.w, L.seg_a, b, g.N);
+    seg_setup(s, make_float3(X.x - O.x, X.y - O.y, X.z - O.z), L.w, CF(kSegA), b, g.N);
     L.Ya = s.Ya;
     L.cp = s.cp;
     L.e = s.e;
@@ -284,7 +300,7 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
     }
     st.steps++;
     if (g.max_steps > 0 && (int)st.steps >= g.max_steps) {
-        L.cls = kStepLimit;
+        CI(kCls) = kStepLimit;
         L.mode = kRayDone;
         return;
     }
@@ -337,7 +353,7 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
             s.A0 = L.A0;
             float th = hit_time(s, ta, tb, d);
             float2 pp = oct_encode(fmaf(th, L.w.x, L.Ya.x), fmaf(th, L.w.y, L.Ya.y), fmaf(th, L.w.z, L.Ya.z));
-            L.cls = kHit;
+            CI(kCls) = kHit;
             L.ux = 0.5f * (pp.x + 1.0f);  // shading uv
             L.uy = 0.5f * (pp.y + 1.0f);
             L.mode = kRayDone;
@@ -363,23 +379,26 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
     float b = (1.0f - (y + 0.5f) / (float)v.H * 2.0f) * v.sb;
     float dx = v.fx + a * v.rx + b * v.ux, dy = v.fy + a * v.ry + b * v.uy, dz = v.fz + a * v.rz + b * v.uz;
     float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-    L.X = make_float3(v.px, v.py, v.pz);
+    const float3 X = make_float3(v.px, v.py, v.pz);
+    CF(kX0) = X.x;
+    CF(kX1) = X.y;
+    CF(kX2) = X.z;
     L.w = make_float3(dx * il, dy * il, dz * il);
-    L.o = v.out_offset + (long long)y * v.W + x;
-    L.cls = kMiss;
+    sh_o[threadIdx.x] = v.out_offset + (long long)y * v.W + x;
+    CI(kCls) = kMiss;
     // eye aligned with a probe (Sec. 4.2): the nearest grid vertex within
     // eye_eps is looked up at oct(w) directly
     const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
-    const float og[3] = {g.ox, g.oy, g.oz}, Xa[3] = {L.X.x, L.X.y, L.X.z};
+    const float og[3] = {g.ox, g.oy, g.oz}, Xa[3] = {X.x, X.y, X.z};
     int iv[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) iv[q] = min(max((int)rintf((Xa[q] - og[q]) / g.spacing), 0), nc[q]);
     int p = iv[0] + g.nx * (iv[1] + g.ny * iv[2]);
     float3 O = corner_pos(g, iv[0], iv[1], iv[2], 0);
-    float ex = L.X.x - O.x, ey = L.X.y - O.y, ez = L.X.z - O.z;
+    float ex = X.x - O.x, ey = X.y - O.y, ez = X.z - O.z;
     if (sqrtf(ex * ex + ey * ey + ez * ez) < g.eye_eps) {
         float2 pp = oct_encode(L.w.x, L.w.y, L.w.z);
-        L.cls = kHit;
+        CI(kCls) = kHit;
         L.probe = p;
         L.ux = 0.5f * (pp.x + 1.0f);
         L.uy = 0.5f * (pp.y + 1.0f);
@@ -388,13 +407,14 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
         L.mode = kRayDone;
         return;
     }
-    L.mode = ray_enter_grid(g, L) ? kCellStart : kRayDone;
+    L.mode = ray_enter_grid(g, X, L.w) ? kCellStart : kRayDone;
 }
 
 template <int RADF>
 __device__ __forceinline__ void write_ray(const GridDev& g, const OutDev& out, const Lane& L) {
-    const long long o = L.o;
-    const bool hit = L.cls == kHit;
+    const long long o = sh_o[threadIdx.x];
+    const int cls = CI(kCls);
+    const bool hit = cls == kHit;
     float3 rgb = make_float3(0.f, 0.f, 0.f);
     if (hit) rgb = shade<RADF>(g, L.probe, L.ux, L.uy);
     if (out.rgb) {
@@ -402,14 +422,14 @@ __device__ __forceinline__ void write_ray(const GridDev& g, const OutDev& out, c
         out.rgb[3 * o + 1] = rgb.y;
         out.rgb[3 * o + 2] = rgb.z;
     }
-    if (out.cls) out.cls[o] = (uint8_t)L.cls;
+    if (out.cls) out.cls[o] = (uint8_t)cls;
     if (out.aux_probe) out.aux_probe[o] = hit ? L.probe : -1;
     if (out.aux_uv) {
         out.aux_uv[2 * o + 0] = hit ? L.ux : 0.0f;
         out.aux_uv[2 * o + 1] = hit ? L.uy : 0.0f;
     }
     if (out.hit_texel) out.hit_texel[o] = hit ? L.i + g.N * L.j : -1;
-    if (L.cls == kStepLimit) atomicOr(g.flags, 1u);
+    if (cls == kStepLimit) atomicOr(g.flags, 1u);
 }
 
 // Persistent kernel: every warp pulls 8x4 ray tiles from `queue` and keeps
@@ -429,6 +449,24 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
     int pool_tile = 0, pool_next = 32;  // warp-uniform ray pool: one 8x4 tile
     bool exhausted = false;
     for (;;) {
+        // ---- control round: every transition runs once, in pipeline order,
+        // for all lanes that need it, so lanes reconverge at each stage ----
+        if (L.mode == kRayDone) {
+            write_ray<RADF>(g, out, L);
+            if (COUNT) {
+                const int cls = CI(kCls);
+                const bool eye = cls == kHit && cells == 0;  // eye-aligned lookup
+                acc[0] += st.coarse;
+                acc[1] += st.fine;
+                acc[2] += st.normal;
+                acc[3] += cls == kHit ? 4 : 0;
+                acc[4] += eye ? 1 : cells;
+                acc[5] += eye ? 1 : probes;
+                acc[6] += cls == kHit ? 1 : 0;
+                acc[7] += 1;
+            }
+            L.mode = kIdle;
+        }
         // refill idle lanes from the warp's pool (warp-synchronous)
         unsigned idle = __ballot_sync(kFull, L.mode == kIdle);
         while (idle != 0u && !exhausted) {
@@ -448,7 +486,7 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
             if (L.mode == kIdle && rank < avail) {
                 st = Stats<COUNT>();
                 cells = probes = 0;
-                start_ray(g, vb, pool_tile, pool_next + rank, L);
+                start_ray(g, vb, pool_tile, pool_next + rank, L);  // kRayDone rays are written next round
             }
             pool_next += min(__popc(idle), avail);
             idle = __ballot_sync(kFull, L.mode == kIdle);
@@ -456,82 +494,63 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
         if (exhausted && L.mode == kIdle) L.mode = kExit;
         if (__all_sync(kFull, L.mode == kExit)) break;
 
-        // Transitions are expensive and divergent: a lane that needs one waits
-        // until kBatchPct % of the busy lanes do (or none walks), so the
-        // set-up code runs for many lanes at once.
-        const bool pending = L.mode != kWalk && L.mode != kIdle && L.mode != kExit;
-        const unsigned pend = __ballot_sync(kFull, pending);
-        const unsigned walk = __ballot_sync(kFull, L.mode == kWalk);
-        if (walk != 0u && 100 * __popc(pend) < kBatchPct * __popc(pend | walk)) {
-#pragma unroll 1
-            for (int r = 0; r < kWalkSteps && L.mode == kWalk; ++r) walk_step<NRMF, COUNT>(g, L, st);
-            continue;
+        if (L.mode == kSegEnd) {  // MISS on this segment: next segment, or the probe is a MISS
+            if (CI(kSegFinal)) {
+                L.mode = kNextCell;
+            } else {
+                CI(kSegI) += 1;
+                CF(kSegA) = CF(kSegB);
+                L.mode = kSegStart;
+            }
+        }
+        if (L.mode == kUnknownRes) {  // UNKNOWN falls through to the next probe of the cage
+            const int q = CI(kQ) + 1;
+            CI(kQ) = q;
+            if (q == 8) {
+                CI(kCbits) |= 0x200;  // saw UNKNOWN
+                L.mode = kNextCell;
+            } else {
+                L.mode = kProbeStart;
+            }
+        }
+        if (L.mode == kNextCell) {
+            const int cbits = CI(kCbits);
+            if (cbits & 0x100) {  // last cell
+                CI(kCls) = (cbits & 0x200) ? kUnknown : kMiss;
+                L.mode = kRayDone;  // written at the next control round
+            } else {
+                int ax = (cbits >> 6) & 3;
+                int st_ax = step_of(cbits, ax);
+                if (ax == 0) CI(kC0) += st_ax;
+                else if (ax == 1) CI(kC1) += st_ax;
+                else CI(kC2) += st_ax;
+                CF(kTin) = CF(kTout);
+                L.mode = kCellStart;
+            }
+        }
+        if (L.mode == kCellStart) {
+            ++cells;
+            cell_start(g, L);
+            L.mode = kProbeStart;
+        }
+        if (L.mode == kProbeStart) {
+            ++probes;
+            probe_start(g, L);
+            L.mode = kSegStart;
+        }
+        if (L.mode == kSegStart) {
+            seg_start(g, L);
+            L.mode = kWalk;
         }
 
-        // transitions: chain until the lane walks again or its ray is done
-        while (L.mode != kWalk && L.mode != kIdle && L.mode != kExit) {
-            switch (L.mode) {
-                case kCellStart:
-                    ++cells;
-                    cell_start(g, L);
-                    L.mode = kProbeStart;
-                    break;
-                case kProbeStart:
-                    ++probes;
-                    probe_start(g, L);
-                    L.mode = kSegStart;
-                    break;
-                case kSegStart:
-                    seg_start(g, L);
-                    L.mode = kWalk;
-                    break;
-                case kSegEnd:  // MISS on this segment: next segment, or the probe is a MISS
-                    if (L.seg_final) {
-                        L.mode = kNextCell;
-                    } else {
-                        ++L.segi;
-                        L.seg_a = L.seg_b;
-                        L.mode = kSegStart;
-                    }
-                    break;
-                case kUnknownRes:  // UNKNOWN falls through to the next probe of the cage
-                    if (++L.q == 8) {
-                        L.cbits |= 0x200;  // saw UNKNOWN
-                        L.mode = kNextCell;
-                    } else {
-                        L.mode = kProbeStart;
-                    }
-                    break;
-                case kNextCell:
-                    if (L.cbits & 0x100) {  // last cell
-                        L.cls = (L.cbits & 0x200) ? kUnknown : kMiss;
-                        L.mode = kRayDone;
-                    } else {
-                        int ax = (L.cbits >> 6) & 3;
-                        int st_ax = step_of(L.cbits, ax);
-                        if (ax == 0) L.c0 += st_ax;
-                        else if (ax == 1) L.c1 += st_ax;
-                        else L.c2 += st_ax;
-                        L.t_in = L.t_out;
-                        L.mode = kCellStart;
-                    }
-                    break;
-                default:  // kRayDone
-                    write_ray<RADF>(g, out, L);
-                    if (COUNT) {
-                        acc[0] += st.coarse;
-                        acc[1] += st.fine;
-                        acc[2] += st.normal;
-                        acc[3] += L.cls == kHit ? 4 : 0;
-                        const bool eye = L.cls == kHit && cells == 0;  // eye-aligned lookup
-                        acc[4] += eye ? 1 : cells;
-                        acc[5] += eye ? 1 : probes;
-                        acc[6] += L.cls == kHit ? 1 : 0;
-                        acc[7] += 1;
-                    }
-                    L.mode = kIdle;
-                    break;
-            }
+        // ---- walk phase: one texel visit per walking lane per step, until
+        // kBatchPct % of the busy lanes wait for a transition ----
+        const int busy = __popc(__ballot_sync(kFull, L.mode != kIdle && L.mode != kExit));
+#pragma unroll 1
+        for (int r = 0; r < kWalkSteps; ++r) {
+            if (L.mode == kWalk) walk_step<NRMF, COUNT>(g, L, st);
+            const int walking = __popc(__ballot_sync(kFull, L.mode == kWalk));
+            if (100 * (busy - walking) >= kBatchPct * busy) break;
         }
     }
     if (COUNT) {
