@@ -119,7 +119,7 @@ class ClockSampler:
 
 def render_source_sha():
     h = hashlib.sha256()
-    for f in ("render.cu", "lfp_device.cuh"):
+    for f in ("render_stream.cu", "render_trace.cuh", "lfp_device.cuh"):
         with open(os.path.join(ROOT, "paper_2507_14624_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -254,7 +254,7 @@ def run_lfp(args):
     traffic = ncu_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": "render_kernel",
+                "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": "render_stream_kernel",
                 "counters_per_launch": counters}
 
     extra = {}
