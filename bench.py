@@ -139,6 +139,22 @@ def ncu_traffic(workload):
     return None
 
 
+def aggregate_over_ranks(seconds, rays, device=None):
+    """Whole-job throughput under weak scaling: every rank renders its own
+    copy of the workload (no data-path collective); the job time is the
+    slowest rank's, the rays are summed. Without an initialised process group
+    this is the single-process value. Returns (Mrays/s, max seconds, rays)."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        r = torch.tensor([float(rays)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(r, op=dist.ReduceOp.SUM)
+        seconds, rays = t.item(), r.item()
+    return rays / seconds / 1e6, seconds, rays
+
+
 def build_workload(name):
     import synth
     sc, views = synth.workload(name)
@@ -227,13 +243,7 @@ def run_lfp(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     times = [a.elapsed_time(b) for a, b in ev]  # ms, render kernel only
-    t_sum = sum(times) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_sum], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_sum = tt.item()
-    rays = total * args.steps * world
-    value = rays / t_sum / 1e6
+    value, t_sum, rays = aggregate_over_ranks(sum(times) / 1e3, total * args.steps, device=dev)
     ms_launch = sum(times) / len(times)
 
     # e2e through the C ABI: host output buffers, copies inside the timed region
@@ -246,7 +256,8 @@ def run_lfp(args):
     for _ in range(e2e_steps):
         grid.render_to_host(views, rgb_h, cls_h)
     e2e_t = time.perf_counter() - t0
-    e2e = {"value": round(total * e2e_steps * world / e2e_t / 1e6, 3), "unit": "Mrays/s",
+    e2e_value, _, _ = aggregate_over_ranks(e2e_t, total * e2e_steps, device=dev)
+    e2e = {"value": round(e2e_value, 3), "unit": "Mrays/s",
            "h2d_bytes_per_step": int(nv * 72), "d2h_bytes_per_step": int(total * 13)}
 
     peak, peak_src = measured_peaks()
