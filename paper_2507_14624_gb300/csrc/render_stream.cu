@@ -55,25 +55,26 @@ enum Mode : int {
 // for more resident warps.
 struct Lane {
     int mode;
-    float3 w;            // ray direction
     int probe;           // current probe
-    // segment (see Seg): u-parametrised octant line
-    float3 Ya;
-    float cp, e, m0, m1, q0, q1, p00, p01, k0, k1, A0, A1, A2, u_end, tstar;
+    // segment (see Seg): u-parametrised octant line, the fields the walk uses
+    float e, m0, m1, q0, q1, A0, A1, A2;
     int dir0, dir1;
-    int quad;            // bit a set: the segment's octant has p_a >= 0
     const float* dmap;   // this probe's distance map
     const float2* mmap;  // this probe's min/max map
     // walk
     int level, i, j, lo0, hi0, lo1, hi1;
     float ux, uy, u, u1, Pa, D2a;  // after a HIT: (ux, uy) hold the shading uv
-    int I, J, lastc;
-    float uxc, uyc, uec;
 };
 
 // control-round fields in shared memory
-enum ColdF { kX0, kX1, kX2, kTin, kTout, kCut0, kCut1, kCut2, kSegA, kSegB, kNumColdF };
-enum ColdI { kC0, kC1, kC2, kCbits, kOrder, kQ, kKq, kSegI, kSegFinal, kCls, kNumColdI };
+enum ColdF {
+    kX0, kX1, kX2, kTin, kTout, kCut0, kCut1, kCut2, kSegA, kSegB,
+    // segment fields used only when a walk descends, decides or ascends
+    kW0, kW1, kW2, kYa0, kYa1, kYa2, kCp, kTstar, kP00, kP01, kK0, kK1, kUend,
+    kUxc, kUyc, kUec,  // the low-resolution texel being refined: next crossings, exit
+    kNumColdF
+};
+enum ColdI { kC0, kC1, kC2, kCbits, kOrder, kQ, kKq, kSegI, kSegFinal, kCls, kQuad, kI, kJ, kLastc, kNumColdI };
 // kCbits: step signs (2 bits per axis: 1 +, 2 -), bits 6-7 exit axis, bit 8
 // last cell, bit 9 saw UNKNOWN. kOrder: corner of rank q in bits [3q, 3q + 3).
 __shared__ float sh_f[kNumColdF][kStreamThreads];
@@ -83,6 +84,8 @@ __shared__ long long sh_o[kStreamThreads];  // output index of the lane's ray
 __device__ __forceinline__ float& CF(int f) { return sh_f[f][threadIdx.x]; }
 __device__ __forceinline__ int& CI(int f) { return sh_i[f][threadIdx.x]; }
 __device__ __forceinline__ float3 ray_X() { return make_float3(CF(kX0), CF(kX1), CF(kX2)); }
+__device__ __forceinline__ float3 ray_w() { return make_float3(CF(kW0), CF(kW1), CF(kW2)); }
+__device__ __forceinline__ float3 seg_Ya() { return make_float3(CF(kYa0), CF(kYa1), CF(kYa2)); }
 
 __device__ __forceinline__ int step_of(int bits, int a) {
     int v = (bits >> (2 * a)) & 3;
@@ -124,11 +127,11 @@ __device__ __forceinline__ bool ray_enter_grid(const GridDev& g, float3 X, float
 }
 
 // Cell c: its exit (3D DDA) and its cage order, nearest corner to the entry first.
-__device__ __forceinline__ void cell_start(const GridDev& g, const Lane& L) {
+__device__ __forceinline__ void cell_start(const GridDev& g) {
     const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
     const float og[3] = {g.ox, g.oy, g.oz};
-    const float3 X = ray_X();
-    const float Xa[3] = {X.x, X.y, X.z}, Wa[3] = {L.w.x, L.w.y, L.w.z};
+    const float3 X = ray_X(), w = ray_w();
+    const float Xa[3] = {X.x, X.y, X.z}, Wa[3] = {w.x, w.y, w.z};
     const int c[3] = {CI(kC0), CI(kC1), CI(kC2)};
     const int cbits = CI(kCbits);
     float tm[3];
@@ -150,7 +153,7 @@ __device__ __forceinline__ void cell_start(const GridDev& g, const Lane& L) {
     CI(kCbits) = (cbits & 0x23f) | (ax << 6) | (last ? 0x100 : 0);
     CF(kTout) = last ? kInf : tax;
     const float t_in = CF(kTin);
-    float3 P = make_float3(fmaf(t_in, L.w.x, X.x), fmaf(t_in, L.w.y, X.y), fmaf(t_in, L.w.z, X.z));
+    float3 P = make_float3(fmaf(t_in, w.x, X.x), fmaf(t_in, w.y, X.y), fmaf(t_in, w.z, X.z));
     CI(kOrder) = (int)cage_order(g, c[0], c[1], c[2], P);
     CI(kQ) = 0;
 }
@@ -162,11 +165,11 @@ __device__ __forceinline__ void probe_start(const GridDev& g, Lane& L) {
     CI(kKq) = kq;
     L.probe = corner_index(g, c0, c1, c2, kq);
     float3 O = corner_pos(g, c0, c1, c2, kq);
-    const float3 X = ray_X();
+    const float3 X = ray_X(), w = ray_w();
     const float t0 = CF(kTin), t1 = CF(kTout);
-    float cx = L.w.x != 0.0f ? (O.x - X.x) * __frcp_rn(L.w.x) : kInf;
-    float cy = L.w.y != 0.0f ? (O.y - X.y) * __frcp_rn(L.w.y) : kInf;
-    float cz = L.w.z != 0.0f ? (O.z - X.z) * __frcp_rn(L.w.z) : kInf;
+    float cx = w.x != 0.0f ? (O.x - X.x) * __frcp_rn(w.x) : kInf;
+    float cy = w.y != 0.0f ? (O.y - X.y) * __frcp_rn(w.y) : kInf;
+    float cz = w.z != 0.0f ? (O.z - X.z) * __frcp_rn(w.z) : kInf;
     cx = (cx > t0 && cx < t1) ? cx : kInf;
     cy = (cy > t0 && cy < t1) ? cy : kInf;
     cz = (cz > t0 && cz < t1) ? cz : kInf;
@@ -180,10 +183,11 @@ __device__ __forceinline__ void probe_start(const GridDev& g, Lane& L) {
 // Low-resolution index box of the segment's quadrant.
 __device__ __forceinline__ void coarse_box(const GridDev& g, Lane& L) {
     const int hm = g.M / 2;
-    L.lo0 = (L.quad & 1) ? hm : 0;
-    L.hi0 = (L.quad & 1) ? g.M - 1 : hm - 1;
-    L.lo1 = (L.quad & 2) ? hm : 0;
-    L.hi1 = (L.quad & 2) ? g.M - 1 : hm - 1;
+    const int quad = CI(kQuad);
+    L.lo0 = (quad & 1) ? hm : 0;
+    L.hi0 = (quad & 1) ? g.M - 1 : hm - 1;
+    L.lo1 = (quad & 2) ? hm : 0;
+    L.hi1 = (quad & 2) ? g.M - 1 : hm - 1;
 }
 
 // Segment segi: the octant line (same arithmetic as seg_setup) and the
@@ -196,37 +200,39 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     if (final_seg) b = CF(kTout);
     CF(kSegB) = b;
     float3 O = corner_pos(g, CI(kC0), CI(kC1), CI(kC2), CI(kKq));
-    const float3 X = ray_X();
+    const float3 X = ray_X(), w = ray_w();
     Seg s;
-    seg_setup(s, make_float3(X.x - O.x, X.y - O.y, X.z - O.z), L.w, CF(kSegA), b, g.N);
-    L.Ya = s.Ya;
-    L.cp = s.cp;
+    seg_setup(s, make_float3(X.x - O.x, X.y - O.y, X.z - O.z), w, CF(kSegA), b, g.N);
+    CF(kYa0) = s.Ya.x;
+    CF(kYa1) = s.Ya.y;
+    CF(kYa2) = s.Ya.z;
+    CF(kCp) = s.cp;
+    CF(kTstar) = s.tstar;
+    CF(kP00) = s.p0[0];
+    CF(kP01) = s.p0[1];
+    CF(kK0) = s.k[0];
+    CF(kK1) = s.k[1];
+    CF(kUend) = s.u_end;
+    CI(kQuad) = (s.lo[0] > 0 ? 1 : 0) | (s.lo[1] > 0 ? 2 : 0);
     L.e = s.e;
     L.m0 = s.m[0];
     L.m1 = s.m[1];
     L.q0 = s.q[0];
     L.q1 = s.q[1];
-    L.p00 = s.p0[0];
-    L.p01 = s.p0[1];
-    L.k0 = s.k[0];
-    L.k1 = s.k[1];
     L.A0 = s.A0;
     L.A1 = s.A1;
     L.A2 = s.A2;
-    L.u_end = s.u_end;
-    L.tstar = s.tstar;
     L.dir0 = s.dir[0];
     L.dir1 = s.dir[1];
-    L.quad = (s.lo[0] > 0 ? 1 : 0) | (s.lo[1] > 0 ? 2 : 0);
     L.dmap = g.dist + (size_t)L.probe * g.N * g.N;
     L.mmap = g.mip + (size_t)L.probe * g.M * g.M;
     const int k = g.k, N = g.N;
     L.level = 0;
     coarse_box(g, L);
-    L.i = min(max(texel_of(L.p00, N, L.dir0) / k, L.lo0), L.hi0);
-    L.j = min(max(texel_of(L.p01, N, L.dir1) / k, L.lo1), L.hi1);
+    L.i = min(max(texel_of(s.p0[0], N, L.dir0) / k, L.lo0), L.hi0);
+    L.j = min(max(texel_of(s.p0[1], N, L.dir1) / k, L.lo1), L.hi1);
     L.u = 0.0f;
-    L.u1 = L.u_end;
+    L.u1 = s.u_end;
     L.Pa = L.A0;
     L.D2a = 1.0f;
     L.ux = L.dir0 == 0 ? kInf : fmaxf(fmaf((float)((L.dir0 > 0 ? L.i + 1 : L.i) * k), L.m0, L.q0), 0.0f);
@@ -236,11 +242,12 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
 // tau from the segment start of walk parameter u (infinite past the end)
 __device__ __forceinline__ float lane_tau(const Lane& L, float u) {
     float D = fmaf(-L.e, u, 1.0f);
-    return D > 0.0f ? L.cp * u / D : kInf;
+    return D > 0.0f ? CF(kCp) * u / D : kInf;
 }
 
-__device__ __forceinline__ float lane_r2(const Lane& L, float tau) {
-    float x = fmaf(tau, L.w.x, L.Ya.x), y = fmaf(tau, L.w.y, L.Ya.y), z = fmaf(tau, L.w.z, L.Ya.z);
+__device__ __forceinline__ float lane_r2(float tau) {
+    const float3 w = ray_w(), Ya = seg_Ya();
+    float x = fmaf(tau, w.x, Ya.x), y = fmaf(tau, w.y, Ya.y), z = fmaf(tau, w.z, Ya.z);
     return x * x + y * y + z * z;
 }
 
@@ -266,16 +273,16 @@ __device__ __forceinline__ bool advance(Lane& L, int scale, float ue, float Pb, 
 // decision: continue the low-resolution walk after that texel.
 __device__ __forceinline__ void ascend(const GridDev& g, Lane& L) {
     L.level = 0;
-    L.i = L.I;
-    L.j = L.J;
+    L.i = CI(kI);
+    L.j = CI(kJ);
     coarse_box(g, L);
-    L.ux = L.uxc;
-    L.uy = L.uyc;
-    L.u1 = L.u_end;
-    float ue = L.uec;
+    L.ux = CF(kUxc);
+    L.uy = CF(kUyc);
+    L.u1 = CF(kUend);
+    float ue = CF(kUec);
     float Pb = fmaf(fmaf(L.A2, ue, L.A1), ue, L.A0);
     float Db = fmaf(-L.e, ue, 1.0f);
-    if (L.lastc || !advance(L, g.k, ue, Pb, Db * Db)) L.mode = kSegEnd;
+    if (CI(kLastc) || !advance(L, g.k, ue, Pb, Db * Db)) L.mode = kSegEnd;
 }
 
 // One texel visit (Appendix A low/highResolutionTracing, one step).
@@ -315,25 +322,25 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
         if (!g.two_way) {
             float ta = lane_tau(L, L.u), tb = lane_tau(L, ue);
             float dk = vmax * g.kappa;
-            if (lane_r2(L, fminf(fmaxf(L.tstar, ta), tb)) > dk * dk) {
+            if (lane_r2(fminf(fmaxf(CF(kTstar), ta), tb)) > dk * dk) {
                 L.mode = kUnknownRes;  // every full-resolution texel under it is passed behind
                 return;
             }
         }
-        L.I = L.i;
-        L.J = L.j;
-        L.uxc = L.ux;
-        L.uyc = L.uy;
-        L.uec = ue;
-        L.lastc = last;
+        CI(kI) = L.i;
+        CI(kJ) = L.j;
+        CF(kUxc) = L.ux;
+        CF(kUyc) = L.uy;
+        CF(kUec) = ue;
+        CI(kLastc) = last;
         L.level = 1;
-        L.lo0 = L.I * k;
+        L.lo0 = L.i * k;
         L.hi0 = L.lo0 + k - 1;
-        L.lo1 = L.J * k;
+        L.lo1 = L.j * k;
         L.hi1 = L.lo1 + k - 1;
         L.u1 = ue;
-        L.i = min(max(texel_of(fmaf(L.k0, L.u, L.p00), N, L.dir0), L.lo0), L.hi0);
-        L.j = min(max(texel_of(fmaf(L.k1, L.u, L.p01), N, L.dir1), L.lo1), L.hi1);
+        L.i = min(max(texel_of(fmaf(CF(kK0), L.u, CF(kP00)), N, L.dir0), L.lo0), L.hi0);
+        L.j = min(max(texel_of(fmaf(CF(kK1), L.u, CF(kP01)), N, L.dir1), L.lo1), L.hi1);
         L.ux = L.dir0 == 0 ? kInf : fmaxf(fmaf((float)(L.dir0 > 0 ? L.i + 1 : L.i), L.m0, L.q0), L.u);
         L.uy = L.dir1 == 0 ? kInf : fmaxf(fmaf((float)(L.dir1 > 0 ? L.j + 1 : L.j), L.m1, L.q1), L.u);
         return;
@@ -342,17 +349,18 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
     float ta = lane_tau(L, L.u), tb = lane_tau(L, ue);
     float d = v, dk = d * g.kappa;
     L.mode = kUnknownRes;
-    if (g.two_way || lane_r2(L, fminf(fmaxf(L.tstar, ta), tb)) <= dk * dk) {
+    if (g.two_way || lane_r2(fminf(fmaxf(CF(kTstar), ta), tb)) <= dk * dk) {
         float2 no = NrmTexel<NRMF>::load(g.nrm, (size_t)L.probe * N * N + (size_t)L.j * N + L.i);
         float3 n = oct_decode_unnorm(no.x, no.y);
+        const float3 w = ray_w();
         if (COUNT) st.normal++;
-        if ((n.x * L.w.x + n.y * L.w.y + n.z * L.w.z) < 0.0f) {
+        if ((n.x * w.x + n.y * w.y + n.z * w.z) < 0.0f) {
             Seg s;  // the hit point needs Ya, w and |Ya|^2 only
-            s.Ya = L.Ya;
-            s.w = L.w;
+            s.Ya = seg_Ya();
+            s.w = w;
             s.A0 = L.A0;
             float th = hit_time(s, ta, tb, d);
-            float2 pp = oct_encode(fmaf(th, L.w.x, L.Ya.x), fmaf(th, L.w.y, L.Ya.y), fmaf(th, L.w.z, L.Ya.z));
+            float2 pp = oct_encode(fmaf(th, w.x, s.Ya.x), fmaf(th, w.y, s.Ya.y), fmaf(th, w.z, s.Ya.z));
             CI(kCls) = kHit;
             L.ux = 0.5f * (pp.x + 1.0f);  // shading uv
             L.uy = 0.5f * (pp.y + 1.0f);
@@ -383,7 +391,10 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
     CF(kX0) = X.x;
     CF(kX1) = X.y;
     CF(kX2) = X.z;
-    L.w = make_float3(dx * il, dy * il, dz * il);
+    const float3 w = make_float3(dx * il, dy * il, dz * il);
+    CF(kW0) = w.x;
+    CF(kW1) = w.y;
+    CF(kW2) = w.z;
     sh_o[threadIdx.x] = v.out_offset + (long long)y * v.W + x;
     CI(kCls) = kMiss;
     // eye aligned with a probe (Sec. 4.2): the nearest grid vertex within
@@ -397,7 +408,7 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
     float3 O = corner_pos(g, iv[0], iv[1], iv[2], 0);
     float ex = X.x - O.x, ey = X.y - O.y, ez = X.z - O.z;
     if (sqrtf(ex * ex + ey * ey + ez * ez) < g.eye_eps) {
-        float2 pp = oct_encode(L.w.x, L.w.y, L.w.z);
+        float2 pp = oct_encode(w.x, w.y, w.z);
         CI(kCls) = kHit;
         L.probe = p;
         L.ux = 0.5f * (pp.x + 1.0f);
@@ -407,7 +418,7 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
         L.mode = kRayDone;
         return;
     }
-    L.mode = ray_enter_grid(g, X, L.w) ? kCellStart : kRayDone;
+    L.mode = ray_enter_grid(g, X, w) ? kCellStart : kRayDone;
 }
 
 template <int RADF>
@@ -530,7 +541,7 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
         }
         if (L.mode == kCellStart) {
             ++cells;
-            cell_start(g, L);
+            cell_start(g);
             L.mode = kProbeStart;
         }
         if (L.mode == kProbeStart) {
