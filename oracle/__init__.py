@@ -40,7 +40,7 @@ class _Grid(ctypes.Structure):
                 ("origin", ctypes.c_double * 3), ("spacing", ctypes.c_double),
                 ("N", ctypes.c_int), ("M", ctypes.c_int),
                 ("thickness_rel", ctypes.c_double), ("eye_eps", ctypes.c_double),
-                ("march_mode", ctypes.c_int)]
+                ("march_mode", ctypes.c_int), ("eye_nearest", ctypes.c_int), ("traversal", ctypes.c_int)]
 
 
 class _Probes(ctypes.Structure):
@@ -181,7 +181,7 @@ class Oracle:
     """
 
     def __init__(self, grid, dist, normal, radiance, thickness_rel=1.0, eye_eps=None,
-                 march=MARCH_HIER):
+                 march=MARCH_HIER, eye_nearest=False, traversal=0):
         self.grid = grid
         self.dist = np.ascontiguousarray(dist, np.float32)
         self.normal = np.ascontiguousarray(normal, np.float32)
@@ -190,6 +190,8 @@ class Oracle:
         self.thickness_rel = float(thickness_rel)
         self.eye_eps = float(1e-6 * grid.spacing if eye_eps is None else eye_eps)
         self.march = march
+        self.eye_nearest = int(bool(eye_nearest))
+        self.traversal = int(traversal)
 
     def _g(self, march=None):
         g = _Grid()
@@ -201,6 +203,8 @@ class Oracle:
         g.thickness_rel = self.thickness_rel
         g.eye_eps = self.eye_eps
         g.march_mode = self.march if march is None else march
+        g.eye_nearest = self.eye_nearest
+        g.traversal = self.traversal
         return g
 
     def _pr(self):

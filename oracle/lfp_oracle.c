@@ -53,7 +53,11 @@
  *      ends the cell; UNKNOWN goes to the next probe; a cell whose 8 probes
  *      are all UNKNOWN sets sawUnknown. At grid exit: UNKNOWN if sawUnknown
  *      else MISS.
- *   R6 eye aligned: |X - O| < eye_eps -> HIT, radiance bilinear at oct(w).
+ *   R6 eye aligned: |X - O| < eye_eps -> HIT, radiance bilinear at oct(w)
+ *      (eye_nearest: the listing's texelFetch, the value of the texel
+ *      holding oct(w)).
+ *   Fewer than 8 probes (traversal 1): probes nearest to the eye first, each
+ *      over [0, inf), MISS or UNKNOWN falls through to the next.
  *
  * Texel walk along a segment: inside one octant both octahedral coordinates
  * are ratios of linear functions of t with a common denominator, so the
@@ -79,6 +83,12 @@ typedef struct {
     double thickness_rel;   /* th in R3 */
     double eye_eps;         /* R6 */
     int march_mode;         /* ORC_MARCH_* */
+    int eye_nearest;        /* eye-aligned lookup: 0 bilinear (R6), 1 the texel
+                               holding oct(w) (the listing's texelFetch) */
+    int traversal;          /* 0 grid iterator over cells (Sec. 4.3, grid
+                               iterator); 1 fewer than 8 probes (Sec. 4.3): all
+                               probes nearest to the eye first, each over the
+                               whole ray, MISS or UNKNOWN -> next probe */
 } orc_grid;
 
 typedef struct {
@@ -494,6 +504,10 @@ static int trace_one_probe(const orc_grid* g, const orc_probes* pr, int probe,
         res->texel_j = texel_of(p[1], g->N, 1);
         res->probe = probe;
         res->t_hit = 0.0;
+        if (g->eye_nearest) { /* the texel's own value: sample at its centre */
+            res->uv[0] = (res->texel_i + 0.5) / g->N;
+            res->uv[1] = (res->texel_j + 0.5) / g->N;
+        }
         radiance_bilinear(g, pr, probe, res->uv, res->rgb);
         return ORC_HIT;
     }
@@ -616,12 +630,53 @@ void orc_cage_order(const orc_grid* g, const int c[3], const double P[3], int or
         }
 }
 
+/* Fewer than 8 probes (Sec. 4.3): start from the probe closest to the eye
+ * (ties: lower index); on MISS or UNKNOWN go to the next closest, each probe
+ * over the whole ray [0, inf). No probe decides: UNKNOWN if one said
+ * UNKNOWN, else MISS. */
+static void trace_nearest_probes(const orc_grid* g, const orc_probes* pr, const double X[3], const double w[3],
+                                 orc_result* res) {
+    int P = g->nx * g->ny * g->nz;
+    int* order = (int*)malloc(sizeof(int) * (size_t)P);
+    double* dd = (double*)malloc(sizeof(double) * (size_t)P);
+    for (int k = 0; k < P; ++k) {
+        double O[3];
+        probe_position(g, k, O);
+        double v[3] = {X[0] - O[0], X[1] - O[1], X[2] - O[2]};
+        dd[k] = sqrt(dot3(v, v));
+        order[k] = k;
+    }
+    for (int x = 1; x < P; ++x)
+        for (int y = x; y > 0 && dd[y] < dd[y - 1]; --y) {
+            double td = dd[y]; dd[y] = dd[y - 1]; dd[y - 1] = td;
+            int to = order[y]; order[y] = order[y - 1]; order[y - 1] = to;
+        }
+    int saw_unknown = 0, hit = 0;
+    res->n_cells = 1;
+    for (int k = 0; k < P && !hit; ++k) {
+        res->n_probes++;
+        int r = trace_one_probe(g, pr, order[k], X, w, 0.0, INFINITY, res);
+        if (r == ORC_HIT) hit = 1;
+        if (r == ORC_UNKNOWN) saw_unknown = 1;
+    }
+    free(order);
+    free(dd);
+    if (hit) { res->cls = ORC_HIT; return; }
+    res->cls = saw_unknown ? ORC_UNKNOWN : ORC_MISS;
+    res->probe = -1;
+    res->texel_i = res->texel_j = -1;
+}
+
 /* Trace one ray through the grid. */
 void orc_trace_ray(const orc_grid* g, const orc_probes* pr, const double X[3], const double w[3],
                    orc_result* res) {
     memset(res, 0, sizeof(*res));
     res->probe = -1;
     res->texel_i = res->texel_j = -1;
+    if (g->traversal == 1) {
+        trace_nearest_probes(g, pr, X, w, res);
+        return;
+    }
     orc_cell cells[1024];
     int ncell = orc_grid_cells(g, X, w, cells, 1024);
     int saw_unknown = 0;

@@ -185,9 +185,16 @@ class Scene:
         lib.syn_cast(ctypes.byref(self._cstruct()), n, _ptr(o), _ptr(d), _ptr(t), _ptr(nn), _ptr(rgb), _ptr(prim))
         return t, nn, rgb, prim
 
-    def probe_maps(self, probe_pos: np.ndarray | None = None, N: int | None = None):
+    def probe_maps(self, probe_pos: np.ndarray | None = None, N: int | None = None, normal_mode: str = "surface"):
         """Probe maps for every probe of the grid (or the given positions):
-        dist [P][N][N] f32, normal [P][N][N][3] f32, radiance [P][N][N][3] f32."""
+        dist [P][N][N] f32, normal [P][N][N][3] f32, radiance [P][N][N][3] f32.
+
+        normal_mode "surface": the geometric normal at the texel's surface
+        point; "incoming": the direction in which light from that point
+        arrives at the probe (point -> probe, minus the texel's direction),
+        the content Sec. 5.1 gives its normal map."""
+        if normal_mode not in ("surface", "incoming"):
+            raise ValueError(normal_mode)
         lib = _load()
         pos = self.grid.probe_positions() if probe_pos is None else np.asarray(probe_pos, np.float64)
         pos = np.ascontiguousarray(pos.reshape(-1, 3))
@@ -197,6 +204,8 @@ class Scene:
         nrm = np.empty((P, N, N, 3), np.float32)
         rad = np.empty((P, N, N, 3), np.float32)
         lib.syn_probe_maps(ctypes.byref(self._cstruct()), P, _ptr(pos), N, _ptr(dist), _ptr(nrm), _ptr(rad))
+        if normal_mode == "incoming":
+            nrm[:] = -texel_directions(N).astype(np.float32)[None]
         return dist, nrm, rad
 
     def distance_to_objects(self, p: np.ndarray) -> float:
@@ -418,6 +427,9 @@ def workload(name: str):
              two lights; 32 views with sizes drawn from 640x480 .. 3840x2160
              along a Catmull-Rom path (seed 303); scene seed 3.
     fit      the room grid with seed 4 and 64 views of 800x800 (70 deg).
+    few      2x2x1 probes (the 4-probe scenario of Sec. 4.3), spacing 1.0,
+             N=256, M=16; 16 spheres + 4 boxes, two lights; one 1920x1080
+             view, 70 deg; seed 6.
     """
     if name == "tiny":
         g = Grid(2, 2, 2, 1.0, 64, 16)
@@ -437,6 +449,10 @@ def workload(name: str):
         g = Grid(4, 4, 4, 0.5, 256, 16)
         sc = make_scene(g, 64, 16, [0.7, 0.3], seed=4, accel_cell=0.25)
         views = [random_view(sc, 104 + 1000 * k, 800, 800, 70.0) for k in range(64)]
+    elif name == "few":
+        g = Grid(2, 2, 1, 1.0, 256, 16)
+        sc = make_scene(g, 16, 4, [0.7, 0.3], seed=6)
+        views = [random_view(sc, 106, 1920, 1080, 70.0)]
     else:
         raise ValueError(f"unknown workload {name!r}")
     return sc, views
