@@ -14,7 +14,9 @@ the host cores (cpu_baseline), fwd+adjoint ms/view on the differentiable-fit
 views, and SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lfp|reference]
-                  [--workload room|batched]
+                  [--workload room|batched|fit|few]
+(few: four probes, the nearest-probe traversal Sec. 4.3 gives for fewer than
+8 probes, on the loop-nest kernel.)
 Under torchrun every rank renders its own copy of the workload (weak scaling,
 no collective on the data path); rank 0 prints the JSON line.
 """
@@ -43,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lfp", choices=["lfp", "reference"])
-    ap.add_argument("--workload", default="room", choices=["room", "batched", "fit"])
+    ap.add_argument("--workload", default="room", choices=["room", "batched", "fit", "few"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
@@ -59,6 +61,9 @@ def dist_env():
 def workload_info(name, views, grid):
     if name == "room":
         desc = "room: 4x4x4 probes spacing 0.5, N=256 M=16, FP32 texels, 64 spheres + 16 boxes, 1 view 1920x1080 70deg"
+    elif name == "few":
+        desc = ("few: 2x2x1 probes spacing 1.0 (nearest-probe traversal for fewer than 8 probes), N=256 M=16, "
+                "FP32 texels, 16 spheres + 4 boxes, 1 view 1920x1080 70deg")
     else:
         desc = ("batched: 8x8x4 probes spacing 0.5, N=512 M=32, FP16 radiance+normal, 256 spheres + 64 boxes, "
                 "32 views 640x480..3840x2160 on a Catmull-Rom path, persistent launch")
@@ -117,9 +122,16 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def render_source_sha():
+def kernel_of(workload):
+    """The kernel that renders the workload: the nearest-probe traversal runs
+    on the loop-nest engine, the grid traversal on the streaming engine."""
+    return "render_kernel" if workload == "few" else "render_stream_kernel"
+
+
+def render_source_sha(workload="room"):
     h = hashlib.sha256()
-    for f in ("render_stream.cu", "render_trace.cuh", "lfp_device.cuh"):
+    first = "render.cu" if kernel_of(workload) == "render_kernel" else "render_stream.cu"
+    for f in (first, "render_trace.cuh", "lfp_device.cuh"):
         with open(os.path.join(ROOT, "paper_2507_14624_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -132,7 +144,7 @@ def ncu_traffic(workload):
     try:
         with open(p) as f:
             d = json.load(f)
-        if d.get("source_sha") == render_source_sha():
+        if d.get("source_sha") == render_source_sha(workload):
             return float(d["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -185,7 +197,8 @@ def run_lfp(args):
     sc, views, d, n, r = build_workload(args.workload)
     f16 = args.workload == "batched"
     fmt = lfpk.LFP_TEXEL_F16 if f16 else lfpk.LFP_TEXEL_F32
-    grid = lfpk.ProbeGrid(sc.grid, radiance_fmt=fmt, normal_fmt=fmt)
+    trav = lfp.LFP_TRAVERSAL_NEAREST if args.workload == "few" else lfp.LFP_TRAVERSAL_GRID
+    grid = lfpk.ProbeGrid(sc.grid, radiance_fmt=fmt, normal_fmt=fmt, traversal=trav)
     grid.upload(d, n, r)
     sched = lfpk.LFP_SCHED_PERSISTENT if len(views) > 1 else 0
     arr, nv, total = lfpk.make_views(views)
@@ -265,7 +278,7 @@ def run_lfp(args):
     traffic = ncu_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": "render_stream_kernel",
+                "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": kernel_of(args.workload),
                 "counters_per_launch": counters}
 
     extra = {}
@@ -273,7 +286,7 @@ def run_lfp(args):
         extra["fwd_adj_ms_per_view"] = fwd_adjoint_ms_per_view(torch, lfpk, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        cpu = cpu_baseline(sc, views, d, n, r, budget_s=10.0)
+        cpu = cpu_baseline(sc, views, d, n, r, budget_s=10.0, traversal=int(trav))
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_launch, 4),
@@ -316,11 +329,11 @@ def fwd_adjoint_ms_per_view(torch, lfpk, dev, steps=5):
     return round(e0.elapsed_time(e1) / steps / len(views), 4)
 
 
-def cpu_baseline(sc, views, d, n, r, budget_s=10.0, max_reps=10):
+def cpu_baseline(sc, views, d, n, r, budget_s=10.0, max_reps=10, traversal=0):
     """The FP64 oracle on the host cores, on the same view: whole frames
     (every pixel) repeated until ~budget_s of CPU time."""
     import oracle
-    o = oracle.Oracle(sc.grid, d, n, r)
+    o = oracle.Oracle(sc.grid, d, n, r, traversal=traversal)
     rays, t0, reps = 0, time.perf_counter(), 0
     while reps < max_reps:
         for v in views[:1]:
@@ -343,7 +356,7 @@ def run_reference(args):
         return
     import oracle
     sc, views, d, n, r = build_workload(args.workload)
-    o = oracle.Oracle(sc.grid, d, n, r)
+    o = oracle.Oracle(sc.grid, d, n, r, traversal=1 if args.workload == "few" else 0)
     v = views[0]
     for _ in range(args.warmup):
         o.render(v, pixels=range(0, v.W * v.H, 64))

@@ -62,7 +62,8 @@ enum {
 };
 
 /* Grid of probes (Sec. 3 "probes are placed at the vertices of a uniform 3D grid").
- *   nx, ny, nz >= 2          probes per axis (cells: (nx-1)(ny-1)(nz-1))
+ *   nx, ny, nz >= 2          probes per axis (cells: (nx-1)(ny-1)(nz-1));
+ *                            >= 1 with traversal LFP_TRAVERSAL_NEAREST
  *   origin, spacing > 0      probe (0,0,0) position and grid pitch
  *   N                        full-resolution map side, even, 2..8192
  *   M                        low-resolution map side, even, N % M == 0, M <= N
@@ -74,7 +75,21 @@ enum {
  *                            highResolutionTracing (every crossing -> normal test)
  *   eye_eps                  |X - O| < eye_eps is "eye aligned with a probe"
  *                            (Sec. 4.2, O(1) lookup); 0 -> 1e-6 * spacing
- *   max_steps                cap on texel visits per ray, 0 = none */
+ *   max_steps                cap on texel visits per ray, 0 = none
+ *   eye_lookup               LFP_EYE_BILINEAR (default): the eye-aligned
+ *                            lookup filters like every other hit;
+ *                            LFP_EYE_NEAREST: the value of the texel holding
+ *                            oct(w) (Appendix A traceOneProbe's texel fetch)
+ *   traversal                LFP_TRAVERSAL_GRID (default): grid iterator over
+ *                            the cells, 8-probe cage per cell (Sec. 4.3);
+ *                            LFP_TRAVERSAL_NEAREST: the mode Sec. 4.3 gives
+ *                            for fewer than 8 probes: all probes (at most 8)
+ *                            nearest to the eye first, each traced over the
+ *                            whole ray; MISS or UNKNOWN goes to the next probe.
+ *                            Runs on the loop-nest engine. */
+enum { LFP_EYE_BILINEAR = 0, LFP_EYE_NEAREST = 1 };
+enum { LFP_TRAVERSAL_GRID = 0, LFP_TRAVERSAL_NEAREST = 1 };
+#define LFP_NEAREST_MAX_PROBES 8
 typedef struct {
     int nx, ny, nz;
     float origin[3];
@@ -84,6 +99,8 @@ typedef struct {
     float thickness_rel;
     float eye_eps;
     int max_steps;
+    int eye_lookup;
+    int traversal;
 } lfp_grid_desc;
 
 /* Pinhole camera (the ray (X, w1) of Sec. 3). The ray through pixel (x, y)

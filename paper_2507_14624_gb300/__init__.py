@@ -46,10 +46,12 @@ class ProbeGrid:
     """A probe grid on the current CUDA device (owns one lfp_grid handle).
 
     spec: object with nx, ny, nz, origin, spacing, N, M (e.g. synth.Grid).
+    eye_lookup: lfp.LFP_EYE_BILINEAR / LFP_EYE_NEAREST; traversal:
+    lfp.LFP_TRAVERSAL_GRID / LFP_TRAVERSAL_NEAREST (at most 8 probes).
     """
 
     def __init__(self, spec, radiance_fmt=LFP_TEXEL_F32, normal_fmt=LFP_TEXEL_F32, thickness_rel=1.0,
-                 eye_eps=0.0, max_steps=0):
+                 eye_eps=0.0, max_steps=0, eye_lookup=0, traversal=0):
         d = lfp.lfp_grid_desc()
         d.nx, d.ny, d.nz = spec.nx, spec.ny, spec.nz
         for i in range(3):
@@ -57,6 +59,7 @@ class ProbeGrid:
         d.spacing, d.N, d.M = spec.spacing, spec.N, spec.M
         d.radiance_fmt, d.normal_fmt = radiance_fmt, normal_fmt
         d.thickness_rel, d.eye_eps, d.max_steps = thickness_rel, eye_eps, max_steps
+        d.eye_lookup, d.traversal = eye_lookup, traversal
         self.desc = d
         self.spec = spec
         self.N, self.M = spec.N, spec.M

@@ -96,7 +96,14 @@ size_t rad_bytes(int fmt) { return fmt == LFP_TEXEL_F32 ? 16 : 8; }
 
 lfp_status check_desc(const lfp_grid_desc* d) {
     if (!d) return LFP_ERR_INVALID_ARG;
-    if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 4096 || d->ny > 4096 || d->nz > 4096) return LFP_ERR_INVALID_ARG;
+    if (d->traversal != LFP_TRAVERSAL_GRID && d->traversal != LFP_TRAVERSAL_NEAREST) return LFP_ERR_INVALID_ARG;
+    if (d->eye_lookup != LFP_EYE_BILINEAR && d->eye_lookup != LFP_EYE_NEAREST) return LFP_ERR_INVALID_ARG;
+    if (d->traversal == LFP_TRAVERSAL_NEAREST) {
+        if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nx * d->ny * d->nz > LFP_NEAREST_MAX_PROBES)
+            return LFP_ERR_INVALID_ARG;
+    } else if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 4096 || d->ny > 4096 || d->nz > 4096) {
+        return LFP_ERR_INVALID_ARG;
+    }
     if ((long long)d->nx * d->ny * d->nz > (1LL << 24)) return LFP_ERR_INVALID_ARG;
     if (!(d->spacing > 0.0f) || !std::isfinite(d->spacing) || !finite3(d->origin)) return LFP_ERR_INVALID_ARG;
     if (d->N < 2 || d->N > 8192 || (d->N & 1)) return LFP_ERR_INVALID_ARG;
@@ -137,6 +144,8 @@ GridDev grid_dev(const lfp_grid* g) {
     d.kappa = (float)(1.0 + 4.0 * (double)std::max(s.thickness_rel, 0.0f) / s.N);
     d.eye_eps = s.eye_eps > 0.0f ? s.eye_eps : 1e-6f * s.spacing;
     d.max_steps = s.max_steps;
+    d.eye_nearest = s.eye_lookup == LFP_EYE_NEAREST ? 1 : 0;
+    d.nearest_probes = s.traversal == LFP_TRAVERSAL_NEAREST ? 1 : 0;
     d.dist = g->dist;
     d.mip = g->mip;
     d.nrm = g->nrm;
@@ -187,7 +196,9 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
         if (!u) return LFP_ERR_STATE;
     GridDev gd = grid_dev(g);
     static thread_local ViewBatch vb;  // ~10 KB: keep it off the host stack
-    if (engine == LFP_ENGINE_STREAM && !flat) {
+    // the streaming engine runs the grid traversal with the hierarchical
+    // march; the flat march and the nearest-probe traversal run on the loop nest
+    if (engine == LFP_ENGINE_STREAM && !flat && g->desc.traversal == LFP_TRAVERSAL_GRID) {
         if (g->stream_blocks == 0)
             g->stream_blocks = std::max(1, render_stream_blocks_per_sm(g->desc.radiance_fmt, g->desc.normal_fmt)) *
                                g->sm_count;
@@ -426,7 +437,7 @@ lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const l
     lfp_render_opts c;
     std::memset(&c, 0, sizeof(c));
     c.engine = LFP_ENGINE_STREAM;
-    cand.push_back(c);
+    if (g->desc.traversal == LFP_TRAVERSAL_GRID) cand.push_back(c);
     const int shapes[5][2] = {{8, 4}, {8, 8}, {16, 8}, {16, 16}, {32, 8}};
     for (auto& sh : shapes)
         for (int sched : {LFP_SCHED_TILES, LFP_SCHED_PERSISTENT}) {

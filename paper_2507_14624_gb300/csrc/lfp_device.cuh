@@ -31,6 +31,8 @@ struct GridDev {
     int two_way;              // th < 0: every crossing goes to the normal test
     float eye_eps;
     int max_steps;            // 0 = no cap
+    int eye_nearest;          // eye-aligned lookup returns the texel holding oct(w)
+    int nearest_probes;       // traversal for fewer than 8 probes (Sec. 4.3)
     const float* dist;
     const float2* mip;
     const void* nrm;

@@ -415,6 +415,10 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
         L.uy = 0.5f * (pp.y + 1.0f);
         L.i = texel_of(pp.x, g.N, 1);
         L.j = texel_of(pp.y, g.N, 1);
+        if (g.eye_nearest) {  // the texel's own value: sample at its centre
+            L.ux = (L.i + 0.5f) / g.N;
+            L.uy = (L.j + 0.5f) / g.N;
+        }
         L.mode = kRayDone;
         return;
     }

@@ -402,12 +402,64 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
             res.probe = p;
             res.u = 0.5f * (pp.x + 1.0f);
             res.v = 0.5f * (pp.y + 1.0f);
-            res.texel = texel_of(pp.x, g.N, 1) + g.N * texel_of(pp.y, g.N, 1);
+            const int ti = texel_of(pp.x, g.N, 1), tj = texel_of(pp.y, g.N, 1);
+            res.texel = ti + g.N * tj;
+            if (g.eye_nearest) {  // the texel's own value: sample at its centre
+                res.u = (ti + 0.5f) / g.N;
+                res.v = (tj + 0.5f) / g.N;
+            }
             res.rgb = shade<RADF>(g, p, res.u, res.v);
             cells = 1;
             probes = 1;
             return res;
         }
+    }
+
+    // Fewer than 8 probes (Sec. 4.3): every probe, nearest to the eye first
+    // (ties to the lower index), over the whole ray; MISS or UNKNOWN falls
+    // through to the next probe.
+    if (g.nearest_probes) {
+        const int P = g.nx * g.ny * g.nz;  // <= 8, checked at grid creation
+        float d2[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float3 O = probe_pos(g, k < P ? k : 0);
+            float dx = Xa[0] - O.x, dy = Xa[1] - O.y, dz = Xa[2] - O.z;
+            d2[k] = k < P ? dx * dx + dy * dy + dz * dz : kInf;
+        }
+        unsigned used = 0;
+        bool saw_unknown = false, step_limited = false;
+        cells = 1;
+        for (int q = 0; q < P; ++q) {
+            int pick = -1;
+            float best = kInf;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (!(used >> k & 1u) && k < P && (pick < 0 || d2[k] < best)) {
+                    best = d2[k];
+                    pick = k;
+                }
+            used |= 1u << pick;
+            probes++;
+            Decision dec;
+            trace_probe<NRMF, COUNT, FLAT>(g, r, pick, probe_pos(g, pick), 0.0f, kInf, dec, st, step_limited);
+            if (step_limited) {
+                res.cls = kStepLimit;
+                return res;
+            }
+            if (dec.cls == kHit) {
+                res.cls = kHit;
+                res.probe = pick;
+                res.u = dec.u;
+                res.v = dec.v;
+                res.texel = dec.texel;
+                res.rgb = shade<RADF>(g, pick, res.u, res.v);
+                return res;
+            }
+            if (dec.cls == kUnknown) saw_unknown = true;
+        }
+        res.cls = saw_unknown ? kUnknown : kMiss;
+        return res;
     }
 
     // Grid iterator (Sec. 4.3): 3D DDA over the cells the ray crosses.

@@ -23,6 +23,9 @@ LFP_MARCH_HIER, LFP_MARCH_FLAT = 0, 1
 LFP_SCHED_AUTO, LFP_SCHED_TILES, LFP_SCHED_PERSISTENT = 0, 1, 2
 LFP_ENGINE_AUTO, LFP_ENGINE_STREAM, LFP_ENGINE_NESTED = 0, 1, 2
 LFP_REDUCE_AUTO, LFP_REDUCE_ATOMIC, LFP_REDUCE_WARP, LFP_REDUCE_SORT = 0, 1, 2, 3
+LFP_EYE_BILINEAR, LFP_EYE_NEAREST = 0, 1
+LFP_TRAVERSAL_GRID, LFP_TRAVERSAL_NEAREST = 0, 1
+LFP_NEAREST_MAX_PROBES = 8
 N_COUNTERS = 8
 COUNTER_NAMES = ("coarse", "fine", "normal", "radiance", "cells", "probes", "hits", "rays")
 
@@ -33,7 +36,7 @@ class lfp_grid_desc(ctypes.Structure):
                 ("N", ctypes.c_int), ("M", ctypes.c_int),
                 ("radiance_fmt", ctypes.c_int), ("normal_fmt", ctypes.c_int),
                 ("thickness_rel", ctypes.c_float), ("eye_eps", ctypes.c_float),
-                ("max_steps", ctypes.c_int)]
+                ("max_steps", ctypes.c_int), ("eye_lookup", ctypes.c_int), ("traversal", ctypes.c_int)]
 
 
 class lfp_view(ctypes.Structure):

@@ -48,7 +48,8 @@ def _desc(lfp, **kw):
 
 @pytest.mark.parametrize("field,value", [("nx", 1), ("N", 63), ("M", 3), ("M", 128), ("N", 48 * 0 + 100),
                                          ("spacing", 0.0), ("spacing", float("nan")), ("radiance_fmt", 7),
-                                         ("max_steps", -1), ("eye_eps", -1.0)])
+                                         ("max_steps", -1), ("eye_eps", -1.0), ("eye_lookup", 2),
+                                         ("traversal", 2), ("traversal", -1)])
 def test_invalid_descriptors_are_rejected(lib, field, value):
     d = _desc(lib, **{field: value})
     if field == "N" and value == 100:
@@ -59,6 +60,20 @@ def test_invalid_descriptors_are_rejected(lib, field, value):
     assert h.value is None  # *out is cleared on failure
     b = ctypes.c_ulonglong()
     assert lib.raw_call("lfp_grid_bytes", ctypes.byref(d), ctypes.byref(b)) == lib.LFP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dims,ok", [((1, 1, 1), True), ((2, 1, 1), True), ((2, 2, 1), True), ((2, 2, 2), True),
+                                     ((3, 3, 1), False), ((0, 1, 1), False)])
+def test_nearest_traversal_takes_one_to_eight_probes(lib, dims, ok):
+    """Sec. 4.3's mode for fewer than 8 probes: any 1..8 probes (no cells
+    needed); the grid traversal keeps nx, ny, nz >= 2."""
+    d = _desc(lib, nx=dims[0], ny=dims[1], nz=dims[2], traversal=lib.LFP_TRAVERSAL_NEAREST)
+    b = ctypes.c_ulonglong()
+    want = lib.LFP_OK if ok else lib.LFP_ERR_INVALID_ARG
+    assert lib.raw_call("lfp_grid_bytes", ctypes.byref(d), ctypes.byref(b)) == want
+    d.traversal = lib.LFP_TRAVERSAL_GRID
+    want = lib.LFP_OK if min(dims) >= 2 else lib.LFP_ERR_INVALID_ARG
+    assert lib.raw_call("lfp_grid_bytes", ctypes.byref(d), ctypes.byref(b)) == want
 
 
 def test_null_arguments_are_rejected(lib):
