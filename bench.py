@@ -137,18 +137,38 @@ def render_source_sha(workload="room"):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per launch of the render kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+def ncu_summary(workload):
+    """The committed ncu summary of the render kernel for this workload, if it
+    was taken on the current kernel source; else an empty dict."""
     p = os.path.join(ROOT, "profiles", f"render_{workload}_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         if d.get("source_sha") == render_source_sha(workload):
-            return float(d["dram_bytes_per_launch"])
+            return d
     except Exception:
         pass
-    return None
+    return {}
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch (read + write) from the committed ncu summary, or None."""
+    d = ncu_summary(workload)
+    return float(d["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in d else None
+
+
+def issue_roofline(workload, ms_launch, sm_mhz, n_sm):
+    """The kernel is bound by instruction issue: warp instructions per launch
+    (an ncu count on the current source) over the event-timed launch, against
+    n_sm x 4 schedulers x one warp instruction per clock."""
+    d = ncu_summary(workload)
+    if "warp_inst_per_launch" not in d or not sm_mhz:
+        return None
+    achieved = d["warp_inst_per_launch"] / (ms_launch / 1e3) / 1e9
+    peak = n_sm * 4 * sm_mhz / 1e3
+    return {"achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "G warp-inst/s",
+            "frac": round(achieved / peak, 4), "warp_inst_per_launch": int(d["warp_inst_per_launch"]),
+            "peak_basis": f"{n_sm} SMs x 4 schedulers x {sm_mhz:.0f} MHz (median sampled SM clock)"}
 
 
 def aggregate_over_ranks(seconds, rays, device=None):
@@ -279,7 +299,9 @@ def run_lfp(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": kernel_of(args.workload),
-                "counters_per_launch": counters}
+                "counters_per_launch": counters,
+                "issue": issue_roofline(args.workload, ms_launch, clk.get("sm_mhz"),
+                                        torch.cuda.get_device_properties(dev).multi_processor_count)}
 
     extra = {}
     if not args.no_adjoint and rank == 0:
