@@ -290,3 +290,68 @@ class Oracle:
         uv = _f64(uv).reshape(-1, 2)
         _load().orc_backward(ctypes.byref(self._g()), len(c), _p(g), _p(c), _p(pb), _p(uv), _p(grad))
         return grad
+
+
+# ---------------------------------------------------------------------------
+# multi-scale hierarchy
+# ---------------------------------------------------------------------------
+
+def probe_box(grid):
+    """Closed box spanned by a grid's probes: [origin, origin + spacing (n - 1)]
+    per axis, the float32 positions every consumer sees."""
+    o = np.asarray(grid.origin, np.float32)
+    s = np.float32(grid.spacing)
+    n = np.array([grid.nx - 1, grid.ny - 1, grid.nz - 1], np.float32)
+    return o.astype(np.float64), (o + s * n).astype(np.float32).astype(np.float64)
+
+
+def pick_level(levels, X):
+    """Level that traces a ray starting at X in a multi-scale hierarchy of
+    probe grids (the "multi-scale, implicit representations" of the abstract,
+    the hierarchical scene representation of the teaser figure): the finest
+    level (smallest spacing, ties to the lower index) whose probe box contains
+    X; if none does, the coarsest (largest spacing, ties to the lower index)."""
+    X = np.asarray(X, np.float64)
+    best = None
+    for k, g in enumerate(levels):
+        lo, hi = probe_box(g)
+        if np.all(X >= lo) and np.all(X <= hi) and (best is None or g.spacing < levels[best].spacing):
+            best = k
+    if best is None:
+        for k, g in enumerate(levels):
+            if best is None or g.spacing > levels[best].spacing:
+                best = k
+    return best
+
+
+class Hierarchy:
+    """FP64 tracer over a multi-scale hierarchy: one Oracle per level; every
+    ray of a view starts at the camera, so the view is traced in the level
+    pick_level gives for the camera position."""
+
+    def __init__(self, levels, maps, **kw):
+        self.levels = list(levels)
+        self.oracles = [Oracle(g, *m, **kw) for g, m in zip(levels, maps)]
+
+    def level_of(self, view):
+        return pick_level(self.levels, view.pos)
+
+    def render(self, view, pixels=None, **kw):
+        k = self.level_of(view)
+        out = self.oracles[k].render(view, pixels, **kw)
+        out["level"] = k
+        return out
+
+    def backward(self, views, grad_rgb, cls, probe, uv):
+        """Per-level radiance gradients ([P_l][N_l][N_l][3] f64) of the views'
+        concatenated pixels (flat, in view order)."""
+        grads = [np.zeros((o.dist.shape[0], g.N, g.N, 3)) for o, g in zip(self.oracles, self.levels)]
+        off = 0
+        for v in views:
+            n = v.W * v.H
+            k = self.level_of(v)
+            sl = slice(off, off + n)
+            grads[k] += self.oracles[k].backward(np.asarray(grad_rgb)[sl], np.asarray(cls)[sl],
+                                                 np.asarray(probe)[sl], np.asarray(uv)[sl])
+            off += n
+        return grads

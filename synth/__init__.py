@@ -456,3 +456,129 @@ def workload(name: str):
     else:
         raise ValueError(f"unknown workload {name!r}")
     return sc, views
+
+
+# ---------------------------------------------------------------------------
+# multi-scale hierarchy: nested probe grids over a street-grid scene
+# ---------------------------------------------------------------------------
+
+def multiscale_levels(scale: int = 1):
+    """Three nested probe grids, coarse to fine (N and M divided by `scale`):
+
+    L0 16x16x4 at spacing 2.0,   N=128, M=8,  origin (0, 0, 0):        x, y in [0, 30]
+    L1 16x16x4 at spacing 0.5,   N=256, M=16, origin (11, 11, 0.5):    x, y in [11, 18.5]
+    L2  8x8x4  at spacing 0.125, N=512, M=32, origin (14.5, 14.5, 0.5): x, y in [14.5, 15.375]
+    """
+    def g(nx, ny, nz, sp, N, M, o):
+        N, M = N // scale, max(2, M // scale)
+        return Grid(nx, ny, nz, sp, N, M, o)
+    return [g(16, 16, 4, 2.0, 128, 8, (0.0, 0.0, 0.0)),
+            g(16, 16, 4, 0.5, 256, 16, (11.0, 11.0, 0.5)),
+            g(8, 8, 4, 0.125, 512, 32, (14.5, 14.5, 0.5))]
+
+
+def street_scene(levels, n_spheres: int = 1024, seed: int = 5, lights=(0.7, 0.3), ambient: float = 0.1,
+                 clearance: float = 0.02) -> Scene:
+    """Street-grid scene around nested probe grids (levels[0] the outermost).
+
+    * Room: levels[0]'s box grown by half its spacing; the floor is its lower z.
+    * 64 x 64 lots at pitch 0.5 over the room's floor, centres at odd multiples
+      of 0.25, one box per lot standing on the floor: footprint half-extents
+      U[0.08, 0.22] (so no box reaches an x or y that is a multiple of 0.5,
+      where the two outer levels' probes sit); lots in every 8th pair of rows
+      and columns are streets (height U[0.1, 0.6]), the rest buildings
+      (U[0.5, 6.0]); lots under the innermost level's box are a plaza (height
+      U[0.05, 0.4], below its lowest probe).
+    * Spheres radius U[0.05, 0.2], centre uniform in the room, redrawn while
+      within `clearance` of any probe of any level. Albedo U[0,1]^3; lights
+      directional, uniform on the upper hemisphere.
+    """
+    rng = SplitMix64(seed)
+    g0 = levels[0]
+    margin = 0.5 * g0.spacing
+    room = np.concatenate([g0.lo() - margin, g0.hi() + margin]).astype(np.float64)
+    wall_albedo = np.array([[rng.uniform() for _ in range(3)] for _ in range(6)], np.float64)
+    probes = np.concatenate([g.probe_positions() for g in levels])
+    inner_lo, inner_hi = levels[-1].lo(), levels[-1].hi()
+    n_lots = int(round((room[3] - room[0]) / 0.5))
+    boxes = []
+    for j in range(n_lots):
+        for i in range(n_lots):
+            c = np.array([room[0] + 0.25 + 0.5 * i, room[1] + 0.25 + 0.5 * j])
+            hx, hy = rng.uniform(0.08, 0.22), rng.uniform(0.08, 0.22)
+            street = (i % 8) in (3, 4) or (j % 8) in (3, 4)
+            plaza = (c[0] + 0.25 >= inner_lo[0] - 0.25 and c[0] - 0.25 <= inner_hi[0] + 0.25 and
+                     c[1] + 0.25 >= inner_lo[1] - 0.25 and c[1] - 0.25 <= inner_hi[1] + 0.25)
+            h = rng.uniform(0.05, 0.4) if plaza else (rng.uniform(0.1, 0.6) if street else rng.uniform(0.5, 6.0))
+            alb = [rng.uniform() for _ in range(3)]
+            boxes.append([c[0] - hx, c[1] - hy, room[2], c[0] + hx, c[1] + hy, room[2] + h, *alb])
+    spheres = []
+    while len(spheres) < n_spheres:
+        r = rng.uniform(0.05, 0.2)
+        c = np.array([rng.uniform(room[a], room[a + 3]) for a in range(3)])
+        alb = [rng.uniform() for _ in range(3)]
+        if np.all(np.linalg.norm(probes - c, axis=1) - r >= clearance):
+            spheres.append([*c, r, *alb])
+    lts = []
+    for inten in lights:
+        z = rng.uniform()
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        s = math.sqrt(max(0.0, 1.0 - z * z))
+        lts.append([s * math.cos(phi), s * math.sin(phi), z, float(inten)])
+    sph = np.ascontiguousarray(np.array(spheres, np.float64).reshape(-1, 7))
+    bxs = np.ascontiguousarray(np.array(boxes, np.float64).reshape(-1, 9))
+    return Scene(grid=g0, spheres=sph, boxes=bxs, room=room, wall_albedo=wall_albedo,
+                 lights=np.ascontiguousarray(np.array(lts, np.float64).reshape(-1, 4)), ambient=ambient,
+                 seed=seed, accel=_build_accel(sph, bxs, room, 0.5))
+
+
+def level_scene(scene: Scene, grid: Grid) -> Scene:
+    """The same scene with another probe grid (for its probe maps and cameras)."""
+    from dataclasses import replace
+    return replace(scene, grid=grid)
+
+
+def _box_contains(g: Grid, p, shrink: float = 0.0) -> bool:
+    lo, hi = g.lo(), g.hi()
+    c, h = 0.5 * (lo + hi), 0.5 * (hi - lo) * (1.0 - shrink)
+    return bool(np.all(p >= c - h) and np.all(p <= c + h))
+
+
+def multiscale_views(scene: Scene, levels, seed: int, n_views: int, sizes, fov_y_deg: float = 70.0,
+                     clearance: float = 0.05):
+    """Views cycling over the levels: view k starts inside level k % L's probe
+    box shrunk by 10 % and outside the next finer level's box, so every level
+    is the finest one containing some cameras; yaw U[0, 2pi), pitch
+    U[-30, 30] deg, redrawn while within `clearance` of an object."""
+    rng = SplitMix64(seed)
+    views = []
+    for k in range(n_views):
+        lev = k % len(levels)
+        g = levels[lev]
+        lo, hi = g.lo(), g.hi()
+        c, h = 0.5 * (lo + hi), 0.5 * (hi - lo) * 0.9
+        W, H = sizes[k % len(sizes)]
+        while True:
+            p = np.array([float(np.float32(rng.uniform(c[a] - h[a], c[a] + h[a]))) for a in range(3)])
+            yaw = rng.uniform(0.0, 2.0 * math.pi)
+            pitch = math.radians(rng.uniform(-30.0, 30.0))
+            if lev + 1 < len(levels) and _box_contains(levels[lev + 1], p):
+                continue
+            if scene.distance_to_objects(p) >= clearance:
+                views.append(look_view(p, yaw, pitch, fov_y_deg, W, H))
+                break
+    return views
+
+
+def multiscale_workload(scale: int = 1, n_views: int = 64):
+    """(scene, levels, views): the street-grid scene (4096 boxes, 1024
+    spheres, seed 5), the three nested levels and `n_views` mixed-resolution
+    views (sizes drawn from 640x480 .. 3840x2160 with seed 305, divided by
+    `scale`; cameras seed 505)."""
+    levels = multiscale_levels(scale)
+    sc = street_scene(levels, seed=5)
+    rng = SplitMix64(305)
+    sizes = [BATCH_SIZES[int(rng.uniform() * 4) % 4] for _ in range(n_views)]
+    sizes = [(max(1, W // scale), max(1, H // scale)) for W, H in sizes]
+    views = multiscale_views(sc, levels, 505, n_views, sizes)
+    return sc, levels, views
