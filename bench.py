@@ -14,7 +14,7 @@ the host cores (cpu_baseline), fwd+adjoint ms/view on the differentiable-fit
 views, and SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lfp|reference]
-                  [--workload room|batched|fit|few]
+                  [--workload room|batched|fit|few|multiscale]
 (few: four probes, the nearest-probe traversal Sec. 4.3 gives for fewer than
 8 probes, on the loop-nest kernel.)
 Under torchrun every rank renders its own copy of the workload (weak scaling,
@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lfp", choices=["lfp", "reference"])
-    ap.add_argument("--workload", default="room", choices=["room", "batched", "fit", "few"])
+    ap.add_argument("--workload", default="room", choices=["room", "batched", "fit", "few", "multiscale"])
+    ap.add_argument("--views", type=int, default=64, help="multiscale: number of views (64 in the configuration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
@@ -377,6 +378,8 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    if args.workload == "multiscale":
+        return run_reference_multiscale(args)
     sc, views, d, n, r = build_workload(args.workload)
     o = oracle.Oracle(sc.grid, d, n, r, traversal=1 if args.workload == "few" else 0)
     v = views[0]
@@ -394,6 +397,200 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
             "config": workload_info(args.workload, views, sc.grid), "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+MULTISCALE_DESC = ("multiscale: 3 nested grids 16x16x4@2.0 N=128 M=8, 16x16x4@0.5 N=256 M=16, 8x8x4@0.125 N=512 "
+                   "M=32, FP16 radiance+normal, FP32 distance; street grid of 4096 boxes + 1024 spheres; 64 views "
+                   "640x480..3840x2160, each traced in the finest level holding its camera")
+
+
+def build_multiscale(lfpk, keep_maps, n_views=64):
+    """The street scene, its three levels uploaded level by level (host maps
+    dropped after upload unless kept for the oracle), the views."""
+    import synth
+    sc, levels, views = synth.multiscale_workload(scale=1, n_views=n_views)
+    grids, maps = [], []
+    for g in levels:
+        d, n, r = synth.level_scene(sc, g).probe_maps()
+        pg = lfpk.ProbeGrid(g, radiance_fmt=lfpk.LFP_TEXEL_F16, normal_fmt=lfpk.LFP_TEXEL_F16)
+        pg.upload(d, n, r)
+        grids.append(pg)
+        maps.append((d, n, r) if keep_maps else None)
+    return sc, levels, views, lfpk.ProbeHierarchy(grids), maps
+
+
+def run_multiscale(args):
+    """Multi-scale hierarchy: one step = one lfp_render_levels call over the 64
+    views (one persistent launch per level, replayed from a CUDA graph);
+    fwd+adjoint ms per view reported beside it."""
+    import numpy as np
+    import torch
+    import paper_2507_14624_gb300 as lfpk
+    from paper_2507_14624_gb300 import lfp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    want_cpu = not args.no_cpu_baseline and rank == 0 and world == 1
+    sc, levels, views, h, maps = build_multiscale(lfpk, keep_maps=want_cpu, n_views=args.views)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    arr, nv, total = lfpk.make_views(views)
+    lev = h.level_of(views)
+    launches_per_step = len(set(lev))
+    graph, out = h.render_graph(views, aux=False)
+
+    cnt = torch.zeros(lfp.N_COUNTERS, dtype=torch.int64, device=dev)
+    oc = lfp.lfp_outputs()
+    oc.rgb, oc.cls, oc.counters = out["rgb"].data_ptr(), out["cls"].data_ptr(), cnt.data_ptr()
+    lfp.lfp_render_levels(h.handles, arr, nv, oc, None, lfpk._stream_handle(stream))
+    torch.cuda.synchronize()
+    counters = dict(zip(lfp.COUNTER_NAMES, (int(x) for x in cnt.cpu().tolist())))
+    alg_bytes = bytes_model(counters, True, True)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        graph.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        graph.replay()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    value, _, _ = aggregate_over_ranks(sum(times) / 1e3, total * args.steps, device=dev)
+    ms_step = sum(times) / len(times)
+
+    # fwd (with aux) + adjoint into per-level gradients, per view
+    fo = h.render(views, aux=True)
+    grad_rgb = torch.randn_like(fo["rgb"])
+    grads = [torch.zeros((g.n_probes, g.N, g.N, 3), dtype=torch.float32, device=dev) for g in h.grids]
+    for _ in range(2):
+        fo = h.render(views, aux=True)
+        h.render_backward(views, grad_rgb, fo["cls"], fo["probe"], fo["uv"], grads)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        fo = h.render(views, aux=True)
+        h.render_backward(views, grad_rgb, fo["cls"], fo["probe"], fo["uv"], grads)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_adj = e0.elapsed_time(e1) / 3 / len(views)
+    del fo, grads, grad_rgb
+
+    # e2e through the public API: render, then rgb + class into pinned host memory
+    rgb_h = torch.empty((total, 3), dtype=torch.float32).pin_memory()
+    cls_h = torch.empty(total, dtype=torch.uint8).pin_memory()
+    e2e_steps = max(3, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        o = h.render(views, aux=False)
+        rgb_h.copy_(o["rgb"], non_blocking=True)
+        cls_h.copy_(o["cls"], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e_value, _, _ = aggregate_over_ranks(e2e_t, total * e2e_steps, device=dev)
+
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    # ncu counts were taken on a 9-view run of the same levels (per ray, scaled
+    # to this step's rays); per launch = per step / launches
+    summ = ncu_summary("multiscale")
+    traffic = summ["dram_bytes_per_ray"] * total / launches_per_step if "dram_bytes_per_ray" in summ else None
+    issue = None
+    if "warp_inst_per_ray" in summ and clk.get("sm_mhz"):
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        ach = summ["warp_inst_per_ray"] * total / (ms_step / 1e3) / 1e9
+        pk = n_sm * 4 * clk["sm_mhz"] / 1e3
+        issue = {"achieved": round(ach, 1), "peak": round(pk, 1), "unit": "G warp-inst/s", "frac": round(ach / pk, 4),
+                 "warp_inst_per_ray": summ["warp_inst_per_ray"],
+                 "peak_basis": f"{n_sm} SMs x 4 schedulers x {clk['sm_mhz']:.0f} MHz (median sampled SM clock)"}
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None if traffic is None else round(traffic),
+                "peak_source": peak_src, "algorithmic_bytes_per_launch": int(alg_bytes / launches_per_step),
+                "algorithmic_bytes_per_step": int(alg_bytes), "kernel": "render_stream_kernel",
+                "counters_per_step": counters, "issue": issue}
+    cpu = None
+    if want_cpu:
+        import oracle
+        ho = oracle.Hierarchy(levels, maps)
+        rng = np.random.default_rng(0)
+        rays, t0 = 0, time.perf_counter()
+        for v in views:
+            pix = np.sort(rng.choice(v.W * v.H, 20000, replace=False))
+            ho.render(v, pix)
+            rays += len(pix)
+            if time.perf_counter() - t0 > 20.0:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(rays / dt / 1e6, 4), "unit": "Mrays/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"20000 random pixels from each of the first {rays // 20000} views"}
+    if rank == 0:
+        per_level = {str(k): sum(1 for x in lev if x == k) for k in sorted(set(lev))}
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32",
+                "data": "synthetic (seeded street-grid scene, probe maps ray-cast)",
+                "config": {"workload": MULTISCALE_DESC, "views": len(views), "rays_per_step": int(total),
+                           "views_per_level": per_level, "l2": "flushed before every timed step (256 MiB write)"},
+                "e2e": {"value": round(e2e_value, 3), "unit": "Mrays/s", "h2d_bytes_per_step": int(nv * 72),
+                        "d2h_bytes_per_step": int(total * 13)},
+                "gpu_launches": launches_per_step * args.steps, "cuda_graph": True, "roofline": roofline,
+                "clocks": clk, "cpu_baseline": cpu, "fwd_adj_ms_per_view": round(fwd_adj, 4)}
+        print(json.dumps(line), flush=True)
+    for g in h.grids:
+        g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference_multiscale(args):
+    """Reference arm on the hierarchy: each step traces 1000 random pixels of
+    every one of the 64 views with the FP64 oracle (64,000 rays, each view in
+    its level)."""
+    import numpy as np
+    import oracle
+    import synth
+    sc, levels, views = synth.multiscale_workload(scale=1, n_views=64)
+    ho = oracle.Hierarchy(levels, [synth.level_scene(sc, g).probe_maps() for g in levels])
+    rng = np.random.default_rng(0)
+
+    def step():
+        for v in views:
+            ho.render(v, np.sort(rng.choice(v.W * v.H, 1000, replace=False)))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = 64000 * args.steps / dt / 1e6
+    cpu = {"value": round(value, 4), "unit": "Mrays/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "1000 random pixels of each of the 64 views per step"}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mrays/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded street-grid scene, probe maps ray-cast)",
+            "config": {"workload": MULTISCALE_DESC, "views": 64}, "cpu_baseline": cpu,
             "e2e": {"value": round(value, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -428,6 +625,8 @@ if __name__ == "__main__":
     a = parse()
     if a.workload == "fit" and a.impl != "reference":
         run_fit(a)
+    elif a.workload == "multiscale" and a.impl != "reference":
+        run_multiscale(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

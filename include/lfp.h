@@ -273,6 +273,37 @@ lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes);
 lfp_status lfp_render_static(lfp_grid* grid, const lfp_view* views, int n_views,
                              const lfp_outputs* out, void* cuda_stream);
 
+/* Multi-scale hierarchy (the "multi-scale, implicit representations" of the
+ * abstract; the hierarchical scene representation of the teaser figure):
+ * several grids of one scene at different spacings, typically nested (coarse
+ * grids over the whole scene, fine grids where the eye goes).
+ *   levels      n_levels (1..16) grid handles on one device, any order
+ * Every ray of a view starts at the camera, so a view is traced in one level:
+ * the finest (smallest spacing, ties to the lower index) whose probe box
+ * [origin, origin + spacing (n - 1)] per axis (closed, float32) holds the
+ * camera position; a camera outside every box uses the coarsest level
+ * (largest spacing, ties to the lower index).
+ *
+ * lfp_pick_levels writes that level for each view (host int32[n_views]).
+ * lfp_render_levels renders every view with its level into the shared flat
+ * outputs (each view at its own out_offset): one lfp_render_ex call per
+ * level that has views, on `cuda_stream`, same options; aux_probe indexes the
+ * probes of the view's level. lfp_render_backward_levels is the adjoint:
+ * grad_radiance is a host array of n_levels device pointers, entry k the
+ * [P_k][N_k][N_k][3] f32 accumulator of level k (may be NULL for a level no
+ * view uses); each level's views go to lfp_render_backward_ex.
+ * Errors: NULL or mismatched arguments, grids on different devices, invalid
+ * views -> LFP_ERR_INVALID_ARG before anything is launched; a failing level
+ * returns its status (levels before it have been launched). */
+lfp_status lfp_pick_levels(lfp_grid* const* levels, int n_levels, const lfp_view* views, int n_views,
+                           int32_t* level_of_view);
+lfp_status lfp_render_levels(lfp_grid* const* levels, int n_levels, const lfp_view* views, int n_views,
+                             const lfp_outputs* out, const lfp_render_opts* opts, void* cuda_stream);
+lfp_status lfp_render_backward_levels(lfp_grid* const* levels, int n_levels, const lfp_view* views,
+                                      int n_views, const float* grad_rgb, const uint8_t* cls,
+                                      const int32_t* aux_probe, const float* aux_uv,
+                                      float* const* grad_radiance, int reduction, void* cuda_stream);
+
 /* Release a grid (NULL-safe; synchronises the device first). */
 void lfp_destroy_grid(lfp_grid* grid);
 

@@ -15,7 +15,7 @@ from .lfp import (LFP_CLASS_HIT, LFP_CLASS_MISS, LFP_CLASS_STEPLIMIT, LFP_CLASS_
                   LFP_ENGINE_STREAM, LFP_MARCH_FLAT, LFP_MARCH_HIER, LFP_SCHED_PERSISTENT, LFP_SCHED_TILES,
                   LFP_TEXEL_F16, LFP_TEXEL_F32, LfpError)
 
-__all__ = ["lfp", "ProbeGrid", "make_views", "render", "LfpError", "LFP_TEXEL_F32", "LFP_TEXEL_F16",
+__all__ = ["lfp", "ProbeGrid", "ProbeHierarchy", "make_views", "render", "render_levels", "LfpError", "LFP_TEXEL_F32", "LFP_TEXEL_F16",
            "LFP_CLASS_MISS", "LFP_CLASS_HIT", "LFP_CLASS_UNKNOWN", "LFP_CLASS_STEPLIMIT",
            "LFP_MARCH_HIER", "LFP_MARCH_FLAT", "LFP_SCHED_TILES", "LFP_SCHED_PERSISTENT", "LFP_ENGINE_STREAM",
            "LFP_ENGINE_NESTED"]
@@ -202,6 +202,83 @@ class ProbeGrid:
         return lfp.lfp_check_flags(self.handle, _stream_handle(stream))
 
 
+class ProbeHierarchy:
+    """Multi-scale hierarchy: ProbeGrids of one scene at several spacings
+    (see lfp_render_levels in include/lfp.h). Each view is traced in the
+    finest level whose probe box holds its camera."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        self.handles = [g.handle for g in self.grids]
+
+    def level_of(self, views) -> list:
+        arr, n, _ = make_views(views)
+        return lfp.lfp_pick_levels(self.handles, arr, n)
+
+    def _outputs(self, total, aux, hit_texel, counters):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = {"rgb": torch.empty((total, 3), dtype=torch.float32, device=dev),
+               "cls": torch.empty(total, dtype=torch.uint8, device=dev)}
+        if aux:
+            out["probe"] = torch.empty(total, dtype=torch.int32, device=dev)
+            out["uv"] = torch.empty((total, 2), dtype=torch.float32, device=dev)
+        if hit_texel:
+            out["texel"] = torch.empty(total, dtype=torch.int32, device=dev)
+        if counters:
+            out["counters"] = torch.zeros(lfp.N_COUNTERS, dtype=torch.int64, device=dev)
+        o = lfp.lfp_outputs()
+        o.rgb, o.cls = out["rgb"].data_ptr(), out["cls"].data_ptr()
+        o.aux_probe = out["probe"].data_ptr() if aux else None
+        o.aux_uv = out["uv"].data_ptr() if aux else None
+        o.hit_texel = out["texel"].data_ptr() if hit_texel else None
+        o.counters = out["counters"].data_ptr() if counters else None
+        return out, o
+
+    def render(self, views, aux=True, hit_texel=False, counters=False, engine=0, stream=None):
+        """Like ProbeGrid.render; `probe` indexes the probes of each view's level."""
+        arr, n, total = make_views(views)
+        out, o = self._outputs(total, aux, hit_texel, counters)
+        opts = lfp.lfp_render_opts()
+        opts.engine = engine
+        lfp.lfp_render_levels(self.handles, arr, n, o, opts, _stream_handle(stream))
+        return out
+
+    def render_graph(self, views, aux=False, stream=None):
+        """One hierarchy render captured in a CUDA graph (outputs reused)."""
+        import torch
+        s = torch.cuda.Stream() if stream is None else stream
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            out = self.render(views, aux=aux, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        arr, n, total = make_views(views)
+        o = lfp.lfp_outputs()
+        o.rgb, o.cls = out["rgb"].data_ptr(), out["cls"].data_ptr()
+        o.aux_probe = out["probe"].data_ptr() if aux else None
+        o.aux_uv = out["uv"].data_ptr() if aux else None
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            lfp.lfp_render_levels(self.handles, arr, n, o, None, _stream_handle(s))
+        graph._lfp_keep = (arr, o)
+        return graph, out
+
+    def render_backward(self, views, grad_rgb, cls, probe, uv, grads=None, reduction=0, stream=None):
+        """Adjoint into one [P][N][N][3] f32 accumulator per level (zeros if
+        None); returns the list."""
+        import torch
+        arr, n, total = make_views(views)
+        if grads is None:
+            grads = [torch.zeros((g.n_probes, g.N, g.N, 3), dtype=torch.float32, device=grad_rgb.device)
+                     for g in self.grids]
+        gr = grad_rgb.contiguous()
+        lfp.lfp_render_backward_levels(self.handles, arr, n, ctypes.c_void_p(gr.data_ptr()),
+                                       ctypes.c_void_p(cls.data_ptr()), ctypes.c_void_p(probe.data_ptr()),
+                                       ctypes.c_void_p(uv.data_ptr()), [t.data_ptr() for t in grads], reduction,
+                                       _stream_handle(stream))
+        return grads
+
+
 def _autograd():
     import torch
 
@@ -224,15 +301,44 @@ def _autograd():
             g = ctx.grid.render_backward(ctx.views, grad_rgb, cls, probe, uv)
             return g, None, None
 
-    return LfpRender
+    class LfpRenderLevels(torch.autograd.Function):
+        """rgb = render over a hierarchy of the per-level radiance tensors."""
+
+        @staticmethod
+        def forward(ctx, hierarchy, views, *radiances):
+            for g, r in zip(hierarchy.grids, radiances):
+                g.set_radiance(r.detach())
+            out = hierarchy.render(views, aux=True)
+            ctx.hierarchy, ctx.views = hierarchy, views
+            ctx.save_for_backward(out["cls"], out["probe"], out["uv"])
+            ctx.mark_non_differentiable(out["cls"])
+            return out["rgb"], out["cls"]
+
+        @staticmethod
+        def backward(ctx, grad_rgb, grad_cls):
+            cls, probe, uv = ctx.saved_tensors
+            grads = ctx.hierarchy.render_backward(ctx.views, grad_rgb, cls, probe, uv)
+            return (None, None, *grads)
+
+    return LfpRender, LfpRenderLevels
 
 
 _LfpRender = None
+_LfpRenderLevels = None
 
 
 def render(radiance, grid: ProbeGrid, views):
     """Differentiable render: radiance [P][N][N][3] f32 CUDA tensor -> (rgb [pixels,3], cls [pixels])."""
-    global _LfpRender
+    global _LfpRender, _LfpRenderLevels
     if _LfpRender is None:
-        _LfpRender = _autograd()
+        _LfpRender, _LfpRenderLevels = _autograd()
     return _LfpRender.apply(radiance, grid, views)
+
+
+def render_levels(radiances, hierarchy: ProbeHierarchy, views):
+    """Differentiable hierarchy render: one radiance tensor [P_l][N_l][N_l][3]
+    per level -> (rgb [pixels,3], cls [pixels])."""
+    global _LfpRender, _LfpRenderLevels
+    if _LfpRender is None:
+        _LfpRender, _LfpRenderLevels = _autograd()
+    return _LfpRenderLevels.apply(hierarchy, views, *radiances)

@@ -81,6 +81,9 @@ def _load():
         "lfp_autotune": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
         "lfp_render_backward": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, vp], i),
         "lfp_render_backward_ex": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, i, vp], i),
+        "lfp_pick_levels": ([P(vp), i, P(lfp_view), i, P(ctypes.c_int32)], i),
+        "lfp_render_levels": ([P(vp), i, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
+        "lfp_render_backward_levels": ([P(vp), i, P(lfp_view), i, vp, vp, vp, vp, P(vp), i, vp], i),
         "lfp_set_radiance": ([vp, vp, vp], i),
         "lfp_check_flags": ([vp, vp], i),
         "lfp_grid_bytes": ([P(lfp_grid_desc), P(ctypes.c_ulonglong)], i),
@@ -155,6 +158,33 @@ def lfp_render_backward_ex(grid, views, n_views, grad_rgb, cls, aux_probe, aux_u
                            stream) -> None:
     _check(_lib.lfp_render_backward_ex(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance,
                                        reduction, stream), "lfp_render_backward_ex")
+
+
+def _handles(grids):
+    arr = (ctypes.c_void_p * len(grids))()
+    for k, g in enumerate(grids):
+        arr[k] = g
+    return arr
+
+
+def lfp_pick_levels(levels, views, n_views) -> list:
+    """Level that traces each view in a multi-scale hierarchy (see include/lfp.h)."""
+    out = (ctypes.c_int32 * n_views)()
+    _check(_lib.lfp_pick_levels(_handles(levels), len(levels), views, n_views, out), "lfp_pick_levels")
+    return list(out)
+
+
+def lfp_render_levels(levels, views, n_views, outputs: lfp_outputs, opts: lfp_render_opts | None, stream) -> None:
+    _check(_lib.lfp_render_levels(_handles(levels), len(levels), views, n_views, ctypes.byref(outputs),
+                                  ctypes.byref(opts) if opts is not None else None, stream), "lfp_render_levels")
+
+
+def lfp_render_backward_levels(levels, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, reduction,
+                               stream) -> None:
+    """grad_radiance: one device pointer (or None) per level."""
+    gp = (ctypes.c_void_p * len(levels))(*grad_radiance)
+    _check(_lib.lfp_render_backward_levels(_handles(levels), len(levels), views, n_views, grad_rgb, cls, aux_probe,
+                                           aux_uv, gp, reduction, stream), "lfp_render_backward_levels")
 
 
 def lfp_set_radiance(grid, dev_radiance, stream) -> None:
