@@ -83,6 +83,7 @@ def _load():
             "orc_backward": ([G, ll, vp, vp, vp, vp, vp], None),
             "orc_bilinear_taps": ([i, vp, vp, vp, vp], None),
             "orc_num_threads": ([], i),
+            "orc_splat_probes": ([ll, vp, vp, vp, i, vp, i, ctypes.c_float, vp, vp, vp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -355,3 +356,28 @@ class Hierarchy:
                                                  np.asarray(probe)[sl], np.asarray(uv)[sl])
             off += n
         return grads
+
+
+# ---------------------------------------------------------------------------
+# probe maps from a point cloud
+# ---------------------------------------------------------------------------
+
+def splat_probes(xyz, rgb, probe_pos, N, normal=None, empty_dist=0.0):
+    """Probe maps from a point cloud (Sec. 4.1 simulated probes, Sec. 5.1
+    probe data generation): per probe and texel the point nearest to the
+    probe; texel binning and ranking in float32 (see lfp_oracle.c).
+    xyz, rgb, normal: [n][3]; probe_pos [P][3]. Returns float32 dist
+    [P][N][N], normal [P][N][N][3] (the points' normals, or the incoming
+    direction -v/|v| when normal is None), radiance [P][N][N][3]."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+    rgb = np.ascontiguousarray(rgb, np.float32).reshape(-1, 3)
+    nrm = None if normal is None else np.ascontiguousarray(normal, np.float32).reshape(-1, 3)
+    pos = np.ascontiguousarray(probe_pos, np.float32).reshape(-1, 3)
+    P = len(pos)
+    dist = np.empty((P, N, N), np.float32)
+    nout = np.empty((P, N, N, 3), np.float32)
+    rad = np.empty((P, N, N, 3), np.float32)
+    lib.orc_splat_probes(ctypes.c_longlong(len(xyz)), _p(xyz), _p(rgb), _p(nrm), P, _p(pos), N,
+                         ctypes.c_float(empty_dist), _p(dist), _p(nout), _p(rad))
+    return dist, nout, rad

@@ -844,3 +844,93 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------
+ * Probe maps from a point cloud (Sec. 4.1, simulated probe data; Sec. 5.1,
+ * probe data generation): every point is taken into the probe's frame
+ * (v = p - O) and projected onto the octahedral map; per texel the point
+ * nearest to the probe is kept. Distance = |v|, radiance = that point's
+ * colour, normal = its normal when the cloud has normals, else the incoming
+ * direction -v / |v| (R8). A texel no point reaches gets distance empty_dist,
+ * radiance 0 and minus its texel-centre direction.
+ *
+ * The texel a point lands in and the ranking of points are integer decisions
+ * made from floating point, so they are taken in float32 with this exact
+ * sequence of correctly rounded operations (no fused multiply-add), the
+ * precision the GPU builder decides in:
+ *   v = p - O per component; q = (v.x*v.x + v.y*v.y) + v.z*v.z;
+ *   s = (|v.x| + |v.y|) + |v.z|, a point with s = 0 or a non-finite q or s is
+ *   skipped; px = v.x / s, py = v.y / s; if v.z < 0:
+ *   (px, py) = ((1 - |py|) sgn px, (1 - |px|) sgn py) with sgn 0 = +1;
+ *   i = min(floor((px + 1) * (N / 2)), N - 1), likewise j from py;
+ *   the smallest q wins, ties to the lower point index; distance = sqrt(q).
+ * OpenMP over probes; each probe keeps its own winner table.
+ */
+static int splat_bin(const float p[3], const float O[3], int N, float* q_out, float v_out[3]) {
+    float vx = p[0] - O[0], vy = p[1] - O[1], vz = p[2] - O[2];
+    float q = vx * vx + vy * vy;
+    q = q + vz * vz;
+    float s = fabsf(vx) + fabsf(vy);
+    s = s + fabsf(vz);
+    if (!(s > 0.0f) || !isfinite(s) || !isfinite(q)) return -1;
+    float px = vx / s, py = vy / s;
+    if (vz < 0.0f) {
+        float fx = (1.0f - fabsf(py)) * (px >= 0.0f ? 1.0f : -1.0f);
+        float fy = (1.0f - fabsf(px)) * (py >= 0.0f ? 1.0f : -1.0f);
+        px = fx;
+        py = fy;
+    }
+    float half = (float)(N / 2);
+    int i = (int)floorf((px + 1.0f) * half), j = (int)floorf((py + 1.0f) * half);
+    if (i > N - 1) i = N - 1;
+    if (j > N - 1) j = N - 1;
+    *q_out = q;
+    v_out[0] = vx;
+    v_out[1] = vy;
+    v_out[2] = vz;
+    return i + N * j;
+}
+
+void orc_splat_probes(long long n_points, const float* xyz, const float* rgb, const float* nrm, int n_probes,
+                      const float* probe_pos, int N, float empty_dist, float* dist, float* normal,
+                      float* radiance) {
+    const long long NN = (long long)N * N;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < n_probes; ++p) {
+        uint64_t* best = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)NN);
+        for (long long t = 0; t < NN; ++t) best[t] = UINT64_MAX;
+        const float* O = probe_pos + 3 * p;
+        for (long long k = 0; k < n_points; ++k) {
+            float q, v[3];
+            int t = splat_bin(xyz + 3 * k, O, N, &q, v);
+            if (t < 0) continue;
+            uint32_t qb;
+            memcpy(&qb, &q, 4);
+            uint64_t key = ((uint64_t)qb << 32) | (uint64_t)(uint32_t)k;
+            if (key < best[t]) best[t] = key;
+        }
+        for (long long t = 0; t < NN; ++t) {
+            long long o = (long long)p * NN + t;
+            if (best[t] == UINT64_MAX) {
+                double pp[2] = {((t % N) + 0.5) / N * 2.0 - 1.0, ((t / N) + 0.5) / N * 2.0 - 1.0}, d[3];
+                orc_oct_decode(pp, d);
+                dist[o] = empty_dist;
+                for (int a = 0; a < 3; ++a) {
+                    normal[3 * o + a] = (float)-d[a];
+                    radiance[3 * o + a] = 0.0f;
+                }
+                continue;
+            }
+            long long k = (long long)(best[t] & 0xffffffffu);
+            float q, v[3];
+            splat_bin(xyz + 3 * k, O, N, &q, v);
+            float r = sqrtf(q);
+            dist[o] = r;
+            for (int a = 0; a < 3; ++a) {
+                normal[3 * o + a] = nrm ? nrm[3 * k + a] : -v[a] / r;
+                radiance[3 * o + a] = rgb[3 * k + a];
+            }
+        }
+        free(best);
+    }
+}

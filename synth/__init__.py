@@ -89,6 +89,8 @@ def _load():
         lib.syn_probe_maps.restype = None
         lib.syn_texel_directions.argtypes = [i, vp]
         lib.syn_texel_directions.restype = None
+        lib.syn_scan.argtypes = [ctypes.POINTER(_SceneC), vp, ll, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
+        lib.syn_scan.restype = None
         _lib = lib
     return _lib
 
@@ -582,3 +584,46 @@ def multiscale_workload(scale: int = 1, n_views: int = 64):
     sizes = [(max(1, W // scale), max(1, H // scale)) for W, H in sizes]
     views = multiscale_views(sc, levels, 505, n_views, sizes)
     return sc, levels, views
+
+
+# ---------------------------------------------------------------------------
+# point clouds: simulated laser scans (the stand-in for the FARO captures)
+# ---------------------------------------------------------------------------
+
+def scan(scene: Scene, positions, n_dirs: int, seed: int, vertical_deg: float = 300.0):
+    """Point cloud of one laser scan per position (Sec. 5.2: the scanner
+    sweeps 360 deg horizontally and `vertical_deg` vertically, so a cone of
+    360 - vertical_deg deg under it stays unseen). Each scan casts n_dirs
+    rays on a spherical Fibonacci lattice with a seeded azimuth phase; every
+    ray's nearest hit is a point with its radiance and surface normal.
+    Returns float32 arrays xyz [n][3], rgb [n][3], normal [n][3] (scans
+    concatenated in order)."""
+    lib = _load()
+    rng = SplitMix64(seed)
+    z_min = -math.cos(math.radians((360.0 - vertical_deg) / 2.0))
+    out = {"xyz": [], "rgb": [], "normal": []}
+    for p in np.asarray(positions, np.float64).reshape(-1, 3):
+        xyz = np.zeros((n_dirs, 3), np.float32)
+        rgb = np.zeros((n_dirs, 3), np.float32)
+        nrm = np.zeros((n_dirs, 3), np.float32)
+        valid = np.zeros(n_dirs, np.uint8)
+        pos = np.ascontiguousarray(p)
+        lib.syn_scan(ctypes.byref(scene._cstruct()), _ptr(pos), n_dirs, rng.uniform(0.0, 2.0 * math.pi), z_min,
+                     _ptr(xyz), _ptr(rgb), _ptr(nrm), _ptr(valid))
+        keep = valid.astype(bool)
+        out["xyz"].append(xyz[keep])
+        out["rgb"].append(rgb[keep])
+        out["normal"].append(nrm[keep])
+    return {k: np.ascontiguousarray(np.concatenate(v)) for k, v in out.items()}
+
+
+def scan_positions(scene: Scene, n: int, seed: int, clearance: float = 0.05):
+    """Scanner positions uniform in the probe cage, redrawn near objects."""
+    rng = SplitMix64(seed)
+    lo, hi = scene.grid.lo(), scene.grid.hi()
+    out = []
+    while len(out) < n:
+        p = np.array([rng.uniform(lo[a], hi[a]) for a in range(3)])
+        if scene.distance_to_objects(p) >= clearance:
+            out.append(p)
+    return np.array(out)
