@@ -14,7 +14,7 @@ the host cores (cpu_baseline), fwd+adjoint ms/view on the differentiable-fit
 views, and SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lfp|reference]
-                  [--workload room|batched|fit|few|multiscale]
+                  [--workload room|batched|fit|few|multiscale|build]
 (few: four probes, the nearest-probe traversal Sec. 4.3 gives for fewer than
 8 probes, on the loop-nest kernel.)
 Under torchrun every rank renders its own copy of the workload (weak scaling,
@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lfp", choices=["lfp", "reference"])
-    ap.add_argument("--workload", default="room", choices=["room", "batched", "fit", "few", "multiscale"])
+    ap.add_argument("--workload", default="room", choices=["room", "batched", "fit", "few", "multiscale", "build"])
     ap.add_argument("--views", type=int, default=64, help="multiscale: number of views (64 in the configuration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -380,6 +380,8 @@ def run_reference(args):
     import oracle
     if args.workload == "multiscale":
         return run_reference_multiscale(args)
+    if args.workload == "build":
+        return run_reference_build(args)
     sc, views, d, n, r = build_workload(args.workload)
     o = oracle.Oracle(sc.grid, d, n, r, traversal=1 if args.workload == "few" else 0)
     v = views[0]
@@ -562,6 +564,31 @@ def run_multiscale(args):
         torch.distributed.destroy_process_group()
 
 
+def run_reference_build(args):
+    """Reference arm of the probe build: the oracle's splat on the host cores,
+    each step the first 1,048,576 points of the cloud into all 64 probes."""
+    import oracle
+    sc, views, pc = build_cloud()
+    P = sc.grid.n_probes
+    sub = slice(0, 1 << 20)
+    for _ in range(args.warmup):
+        oracle.splat_probes(pc["xyz"][:4096], pc["rgb"][:4096], sc.grid.probe_positions(), sc.grid.N)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.splat_probes(pc["xyz"][sub], pc["rgb"][sub], sc.grid.probe_positions(), sc.grid.N)
+    dt = time.perf_counter() - t0
+    value = (1 << 20) * P * args.steps / dt / 1e9
+    cpu = {"value": round(value, 4), "unit": "G pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"the first 1,048,576 points into all {P} probes per step"}
+    line = {"impl": "reference", "metric": "probe build throughput (point x probe pairs per second)",
+            "value": round(value, 4), "unit": "G pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded room scene, simulated laser scans)",
+            "config": {"workload": BUILD_DESC}, "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 4), "unit": "G pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_multiscale(args):
     """Reference arm on the hierarchy: each step traces 1000 random pixels of
     every one of the 64 views with the FP64 oracle (64,000 rays, each view in
@@ -593,6 +620,113 @@ def run_reference_multiscale(args):
             "config": {"workload": MULTISCALE_DESC, "views": 64}, "cpu_baseline": cpu,
             "e2e": {"value": round(value, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+BUILD_DESC = ("build: room grid (4x4x4 probes spacing 0.5, N=256, FP32 texels) filled from a point cloud of 4 "
+              "simulated laser scans x 8,388,608 directions (300 deg vertical), nearest point per texel")
+
+
+def build_cloud():
+    import synth
+    sc, views = synth.workload("room")
+    pc = synth.scan(sc, synth.scan_positions(sc, 4, 2024), 1 << 23, seed=2025)
+    return sc, views, pc
+
+
+def run_build(args):
+    """Point-cloud probe builder: one step = lfp_build_probes_from_points for
+    all 64 probes of the room grid from a device-resident cloud (splat with
+    64-bit atomicMin, resolve, normal encode, radiance pack, min/max map)."""
+    import numpy as np
+    import torch
+    import paper_2507_14624_gb300 as lfpk
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sc, views, pc = build_cloud()
+    dev = torch.device("cuda", local)
+    n_pts = len(pc["xyz"])
+    xyz, rgb = (torch.tensor(pc[k], device=dev) for k in ("xyz", "rgb"))
+    g = lfpk.ProbeGrid(sc.grid)
+    P = g.n_probes
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        g.build_from_points(xyz, rgb)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        g.build_from_points(xyz, rgb)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(times) / len(times)
+    pairs = n_pts * P
+    value, _, _ = aggregate_over_ranks(sum(times) / 1e3, pairs * args.steps / 1e3, device=dev)  # G pairs/s
+
+    # e2e: host cloud in, maps back to host (read_probes + copy)
+    e2e_steps = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.build_from_points(pc["xyz"], pc["rgb"])
+        maps = [t.cpu() for t in g.read_probes()]
+    e2e_t = time.perf_counter() - t0
+    e2e_value, _, _ = aggregate_over_ranks(e2e_t, pairs * e2e_steps / 1e3, device=dev)
+    d2h = sum(t.numel() * 4 for t in maps)
+
+    NN = g.N * g.N
+    # algorithmic HBM bytes of one build: the cloud read once (one chunk), the
+    # (distance, index) table cleared and read (8 + 8 per texel), the winner's
+    # point and colour (24), dist (4), normal and colour staging written and
+    # read (24 + 24), normal and radiance texels written (8 + 16), the
+    # distance map read for the min/max map (4) and the map written
+    alg = n_pts * 12 + P * NN * (8 + 8 + 24 + 4 + 24 + 24 + 8 + 16 + 4) + P * g.M * g.M * 8
+    peak, peak_src = measured_peaks()
+    achieved = alg / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": int(alg), "kernel": "splat_kernel + resolve_kernel",
+                "note": "per build (5 launches); the splat's 64-bit atomics stay in L2"}
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+        sub = slice(0, 1 << 20)
+        t0 = time.perf_counter()
+        oracle.splat_probes(pc["xyz"][sub], pc["rgb"][sub], sc.grid.probe_positions(), sc.grid.N)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round((1 << 20) * P / dt / 1e9, 4), "unit": "G point-probe pairs/s",
+               "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"the first 1,048,576 points of the cloud into all {P} probes"}
+    if rank == 0:
+        line = {"metric": "probe build throughput (point x probe pairs per second)", "value": round(value, 3),
+                "unit": "G pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded room scene, simulated laser scans)",
+                "config": {"workload": BUILD_DESC, "points": n_pts, "probes": P, "N": g.N,
+                           "l2": "flushed before every timed step (256 MiB write)"},
+                "e2e": {"value": round(e2e_value, 3), "unit": "G pairs/s", "h2d_bytes_per_step": int(n_pts * 24),
+                        "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": 6 * args.steps, "roofline": roofline, "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_fit(args):
@@ -627,6 +761,8 @@ if __name__ == "__main__":
         run_fit(a)
     elif a.workload == "multiscale" and a.impl != "reference":
         run_multiscale(a)
+    elif a.workload == "build" and a.impl != "reference":
+        run_build(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

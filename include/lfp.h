@@ -273,6 +273,55 @@ lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes);
 lfp_status lfp_render_static(lfp_grid* grid, const lfp_view* views, int n_views,
                              const lfp_outputs* out, void* cuda_stream);
 
+/* A point cloud, e.g. merged laser scans in one world frame (Sec. 4.1, Sec. 5.1).
+ *   xyz     [n][3] float32 world positions
+ *   rgb     [n][3] float32 colour (stored as the probe radiance)
+ *   normal  [n][3] float32 unit surface normals, or NULL: the builder then
+ *           stores the incoming direction (point -> probe), the content
+ *           Sec. 5.1 gives its normal map
+ *   n       1 .. 2^32 - 1 points
+ *   is_device 1: device pointers, read in place; 0: host pointers, copied
+ *           into temporary device buffers (the call then synchronises) */
+typedef struct {
+    const float* xyz;
+    const float* rgb;
+    const float* normal;
+    long long n;
+    int is_device;
+} lfp_point_cloud;
+
+/* Probe maps of probes [first_probe, first_probe + count) from a point cloud
+ * (Sec. 4.1 simulated probe data: any grid position can become a probe;
+ * Sec. 5.1 probe data generation): every point is moved into the probe's
+ * frame (v = p - O), projected onto the octahedral map, and per texel the
+ * point nearest to the probe is kept: distance |v|, its colour, its normal
+ * (or -v/|v|). Texels no point reaches get distance empty_dist, radiance 0
+ * and normal minus the texel-centre direction (empty_dist 0: any ray through
+ * them passes behind and is UNKNOWN; a large value: they never stop a ray).
+ * The min/max map is rebuilt and the probes count as uploaded.
+ * The texel and the ranking are decided in float32 with this sequence of
+ * correctly rounded operations (no fused multiply-add), so other
+ * implementations following it bin identically:
+ *   v = p - O per component; q = (v.x v.x + v.y v.y) + v.z v.z;
+ *   s = (|v.x| + |v.y|) + |v.z| (s = 0 or non-finite q or s: point skipped);
+ *   r = 1 / s; px = v.x r, py = v.y r; if v.z < 0:
+ *   (px, py) = ((1 - |py|) sgn px, (1 - |px|) sgn py), sgn 0 = +1;
+ *   i = floor((px + 1) (N / 2)) clamped to [0, N - 1], j likewise from py;
+ *   the smallest q wins, ties to the lower point index; distance = sqrt(q).
+ * Work: probes in chunks whose (distance, index) table fits 64 MiB; per chunk
+ * one pass over the points (64-bit atomicMin per point and probe) and one
+ * over the texels. Errors: LFP_ERR_INVALID_ARG (NULL xyz/rgb, range,
+ * n out of range, non-finite empty_dist), LFP_ERR_OOM. */
+lfp_status lfp_build_probes_from_points(lfp_grid* grid, int first_probe, int count, const lfp_point_cloud* cloud,
+                                        float empty_dist, void* cuda_stream);
+
+/* Read probe maps back as float32 device arrays: dist [count][N][N], normal
+ * [count][N][N][3] (unit xyz decoded from the stored octahedral pair),
+ * radiance [count][N][N][3] (from the stored texels: FP16 storage returns
+ * the rounded values). LFP_ERR_STATE if a probe was never filled. */
+lfp_status lfp_read_probes(lfp_grid* grid, int first_probe, int count, float* dist, float* normal, float* radiance,
+                           void* cuda_stream);
+
 /* Multi-scale hierarchy (the "multi-scale, implicit representations" of the
  * abstract; the hierarchical scene representation of the teaser figure):
  * several grids of one scene at different spacings, typically nested (coarse

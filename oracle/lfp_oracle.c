@@ -860,9 +860,9 @@ int orc_num_threads(void) {
  * precision the GPU builder decides in:
  *   v = p - O per component; q = (v.x*v.x + v.y*v.y) + v.z*v.z;
  *   s = (|v.x| + |v.y|) + |v.z|, a point with s = 0 or a non-finite q or s is
- *   skipped; px = v.x / s, py = v.y / s; if v.z < 0:
+ *   skipped; r = 1 / s; px = v.x r, py = v.y r; if v.z < 0:
  *   (px, py) = ((1 - |py|) sgn px, (1 - |px|) sgn py) with sgn 0 = +1;
- *   i = min(floor((px + 1) * (N / 2)), N - 1), likewise j from py;
+ *   i = floor((px + 1) * (N / 2)) clamped to [0, N - 1], likewise j from py;
  *   the smallest q wins, ties to the lower point index; distance = sqrt(q).
  * OpenMP over probes; each probe keeps its own winner table.
  */
@@ -873,7 +873,8 @@ static int splat_bin(const float p[3], const float O[3], int N, float* q_out, fl
     float s = fabsf(vx) + fabsf(vy);
     s = s + fabsf(vz);
     if (!(s > 0.0f) || !isfinite(s) || !isfinite(q)) return -1;
-    float px = vx / s, py = vy / s;
+    float inv = 1.0f / s;
+    float px = vx * inv, py = vy * inv;
     if (vz < 0.0f) {
         float fx = (1.0f - fabsf(py)) * (px >= 0.0f ? 1.0f : -1.0f);
         float fy = (1.0f - fabsf(px)) * (py >= 0.0f ? 1.0f : -1.0f);
@@ -882,8 +883,8 @@ static int splat_bin(const float p[3], const float O[3], int N, float* q_out, fl
     }
     float half = (float)(N / 2);
     int i = (int)floorf((px + 1.0f) * half), j = (int)floorf((py + 1.0f) * half);
-    if (i > N - 1) i = N - 1;
-    if (j > N - 1) j = N - 1;
+    i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
+    j = j < 0 ? 0 : (j > N - 1 ? N - 1 : j);
     *q_out = q;
     v_out[0] = vx;
     v_out[1] = vy;

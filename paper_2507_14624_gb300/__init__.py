@@ -104,6 +104,43 @@ class ProbeGrid:
         if not pl.is_device:  # host planes must outlive the asynchronous copies
             torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
 
+    def build_from_points(self, xyz, rgb, normal=None, first_probe=0, count=None, empty_dist=0.0, stream=None):
+        """Fill probes [first_probe, first_probe + count) from a point cloud
+        (lfp_build_probes_from_points): xyz, rgb, optional normal [n][3]
+        float32, numpy (host) or CUDA tensors (device)."""
+        import numpy as np
+        import torch
+        count = self.n_probes - first_probe if count is None else count
+        pc = lfp.lfp_point_cloud()
+        arrays = [xyz, rgb] + ([normal] if normal is not None else [])
+        if isinstance(xyz, torch.Tensor):
+            keep = [t.contiguous() for t in arrays]
+            for t in keep:
+                if t.dtype != torch.float32 or not t.is_cuda:
+                    raise ValueError("device point clouds must be CUDA float32 tensors")
+            ptr = [t.data_ptr() for t in keep]
+            pc.is_device = 1
+        else:
+            keep = [np.ascontiguousarray(a, dtype=np.float32) for a in arrays]
+            ptr = [a.ctypes.data for a in keep]
+            pc.is_device = 0
+        pc.xyz, pc.rgb = ptr[0], ptr[1]
+        pc.normal = ptr[2] if normal is not None else None
+        pc.n = keep[0].shape[0]
+        lfp.lfp_build_probes_from_points(self.handle, first_probe, count, pc, empty_dist, _stream_handle(stream))
+
+    def read_probes(self, first_probe=0, count=None, stream=None):
+        """(dist [c][N][N], normal [c][N][N][3], radiance [c][N][N][3]) float32 CUDA tensors."""
+        import torch
+        count = self.n_probes - first_probe if count is None else count
+        dev = torch.device("cuda", torch.cuda.current_device())
+        d = torch.empty((count, self.N, self.N), dtype=torch.float32, device=dev)
+        n = torch.empty((count, self.N, self.N, 3), dtype=torch.float32, device=dev)
+        r = torch.empty((count, self.N, self.N, 3), dtype=torch.float32, device=dev)
+        lfp.lfp_read_probes(self.handle, first_probe, count, ctypes.c_void_p(d.data_ptr()),
+                            ctypes.c_void_p(n.data_ptr()), ctypes.c_void_p(r.data_ptr()), _stream_handle(stream))
+        return d, n, r
+
     def set_radiance(self, radiance, stream=None):
         """Replace all probes' radiance from a CUDA float32 tensor [P][N][N][3]."""
         r = radiance.contiguous()

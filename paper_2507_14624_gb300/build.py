@@ -12,7 +12,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblfp.so")
-SOURCES = ["render.cu", "render_stream.cu", "render_static.cu", "support.cu", "api.cu", "levels.cu"]
+SOURCES = ["render.cu", "render_stream.cu", "render_static.cu", "support.cu", "api.cu", "levels.cu",
+           "build_probes.cu"]
 HEADERS = ["lfp_device.cuh", "lfp_internal.h", "render_trace.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -29,6 +29,8 @@ struct lfp_grid {
     unsigned* tile_counter = nullptr;   // persistent-schedule work queue head
     float* staging = nullptr;
     size_t staging_bytes = 0;
+    unsigned long long* keys = nullptr; // point-cloud builder: nearest-point table
+    size_t keys_bytes = 0;
     float* host_rgb = nullptr;          // device buffers behind lfp_render_to_host
     uint8_t* host_cls = nullptr;
     long long host_pixels = 0;
@@ -261,6 +263,7 @@ void destroy(lfp_grid* g) {
     dev_free(g->flags);
     dev_free(g->tile_counter);
     dev_free(g->staging);
+    dev_free(g->keys);
     dev_free(g->host_rgb);
     dev_free(g->host_cls);
     delete g;
@@ -290,6 +293,25 @@ ViewDev view_dev_of(const lfp_view& v, int tile_w, int tile_h, int tile_begin) {
 int check_views_of(const lfp_view* views, int n_views) { return check_views(views, n_views); }
 
 }  // namespace lfp
+
+namespace {
+
+// grow a grid-owned device buffer (synchronising the stream before freeing)
+template <typename T>
+lfp_status ensure(T** buf, size_t* have, size_t need, cudaStream_t s) {
+    if (*have >= need) return LFP_OK;
+    if (*buf) {
+        LFP_CUDA(cudaStreamSynchronize(s));
+        dev_free(*buf);
+        *buf = nullptr;
+        *have = 0;
+    }
+    LFP_TRY(dev_alloc((void**)buf, need));
+    *have = need;
+    return LFP_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -387,6 +409,90 @@ lfp_status lfp_upload_probes(lfp_grid* g, int first_probe, int count, const lfp_
     }
     LFP_CUDA(launch_build_mip(dist_dst, g->mip + (size_t)first_probe * g->desc.M * g->desc.M, count, N, g->desc.M, s));
     for (int p = first_probe; p < first_probe + count; ++p) g->uploaded[p] = 1;
+    return LFP_OK;
+}
+
+lfp_status lfp_build_probes_from_points(lfp_grid* g, int first_probe, int count, const lfp_point_cloud* pc,
+                                        float empty_dist, void* stream) {
+    if (!g || !pc || !pc->xyz || !pc->rgb) return LFP_ERR_INVALID_ARG;
+    if (first_probe < 0 || count < 1 || (long long)first_probe + count > g->P) return LFP_ERR_INVALID_ARG;
+    if (pc->n < 1 || pc->n > 0xffffffffLL || !std::isfinite(empty_dist)) return LFP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = g->desc.N;
+    const size_t NN = (size_t)N * N;
+    const long long n = pc->n;
+    // host clouds are copied into temporary device buffers, freed at the end
+    const float *xyz = pc->xyz, *rgb = pc->rgb, *nrm = pc->normal;
+    float* tmp = nullptr;
+    if (!pc->is_device) {
+        size_t planes = nrm ? 3 : 2;
+        LFP_TRY(dev_alloc((void**)&tmp, planes * n * 12));
+        cudaError_t e = cudaMemcpyAsync(tmp, pc->xyz, n * 12, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + 3 * n, pc->rgb, n * 12, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && nrm) e = cudaMemcpyAsync(tmp + 6 * n, pc->normal, n * 12, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            dev_free(tmp);
+            return LFP_ERR_CUDA;
+        }
+        xyz = tmp;
+        rgb = tmp + 3 * n;
+        nrm = nrm ? tmp + 6 * n : nullptr;
+    }
+    // chunk of probes whose key table fits a 64 MiB slice of L2
+    const int chunk = (int)std::max<size_t>(
+        1, std::min<size_t>(std::min(count, kMaxSplatProbes), (64u << 20) / (NN * 8)));
+    lfp_status st = ensure(&g->keys, &g->keys_bytes, chunk * NN * 8, s);
+    if (st == LFP_OK) st = ensure(&g->staging, &g->staging_bytes, chunk * NN * 24, s);
+    GridDev gd = grid_dev(g);
+    for (int c0 = 0; c0 < count && st == LFP_OK; c0 += chunk) {
+        const int c = std::min(chunk, count - c0), p0 = first_probe + c0;
+        const long long m = (long long)c * NN;
+        float* nrm_st = g->staging;
+        float* rgb_st = g->staging + 3 * m;
+        cudaError_t e = cudaMemsetAsync(g->keys, 0xff, m * 8, s);
+        if (e == cudaSuccess) e = launch_splat(xyz, n, gd, p0, c, g->keys, s);
+        if (e == cudaSuccess)
+            e = launch_resolve(xyz, rgb, nrm, gd, p0, c, g->keys, empty_dist, g->dist + (size_t)p0 * NN, nrm_st,
+                               rgb_st, s);
+        if (e == cudaSuccess)
+            e = launch_encode_normals(nrm_st, (char*)g->nrm + (size_t)p0 * NN * nrm_bytes(g->desc.normal_fmt),
+                                      g->desc.normal_fmt, m, s);
+        if (e == cudaSuccess)
+            e = launch_convert_radiance(rgb_st, (char*)g->rad + (size_t)p0 * NN * rad_bytes(g->desc.radiance_fmt),
+                                        g->desc.radiance_fmt, m, s);
+        if (e != cudaSuccess) st = LFP_ERR_CUDA;
+    }
+    if (st == LFP_OK &&
+        launch_build_mip(g->dist + (size_t)first_probe * NN, g->mip + (size_t)first_probe * g->desc.M * g->desc.M,
+                         count, N, g->desc.M, s) != cudaSuccess)
+        st = LFP_ERR_CUDA;
+    if (tmp) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) st = LFP_ERR_CUDA;
+        dev_free(tmp);
+    }
+    if (st == LFP_OK)
+        for (int p = first_probe; p < first_probe + count; ++p) g->uploaded[p] = 1;
+    return st;
+}
+
+lfp_status lfp_read_probes(lfp_grid* g, int first_probe, int count, float* dist, float* normal, float* radiance,
+                           void* stream) {
+    if (!g || !dist || !normal || !radiance) return LFP_ERR_INVALID_ARG;
+    if (first_probe < 0 || count < 1 || (long long)first_probe + count > g->P) return LFP_ERR_INVALID_ARG;
+    for (int p = first_probe; p < first_probe + count; ++p)
+        if (!g->uploaded[p]) return LFP_ERR_STATE;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t NN = (size_t)g->desc.N * g->desc.N;
+    const long long m = (long long)count * NN;
+    LFP_CUDA(cudaMemcpyAsync(dist, g->dist + (size_t)first_probe * NN, m * 4, cudaMemcpyDeviceToDevice, s));
+    LFP_CUDA(launch_decode_normals((const char*)g->nrm + (size_t)first_probe * NN * nrm_bytes(g->desc.normal_fmt),
+                                   g->desc.normal_fmt, normal, m, s));
+    LFP_CUDA(launch_unpack_radiance((const char*)g->rad + (size_t)first_probe * NN * rad_bytes(g->desc.radiance_fmt),
+                                    g->desc.radiance_fmt, radiance, m, s));
     return LFP_OK;
 }
 

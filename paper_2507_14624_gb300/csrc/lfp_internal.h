@@ -7,6 +7,8 @@
 
 namespace lfp {
 
+constexpr int kMaxSplatProbes = 2048;
+
 struct RenderLaunch {
     int flat;                 // full-resolution march only (Appendix A RayMarching)
     int persistent;           // persistent CTAs pulling tiles from tile_counter
@@ -33,6 +35,19 @@ cudaError_t launch_build_mip(const float* dist, float2* mip, int count, int N, i
 cudaError_t launch_backward(int N, const PixBatch& pb, const float* grad_rgb, const uint8_t* cls,
                             const int32_t* aux_probe, const float* aux_uv, float* grad_rad, int reduction,
                             cudaStream_t s);
+
+// probe maps from a point cloud (build_probes.cu): at most kMaxSplatProbes
+// probes per splat launch (their positions sit in shared memory); keys [count][N][N] set to
+// ~0 by the caller; resolve writes dist into the grid and normal xyz / rgb
+// into staging planes [count][N][N][3]
+cudaError_t launch_splat(const float* xyz, long long n, const GridDev& g, int first, int count,
+                         unsigned long long* keys, cudaStream_t s);
+cudaError_t launch_resolve(const float* xyz, const float* rgb, const float* nrm, const GridDev& g, int first,
+                           int count, const unsigned long long* keys, float empty_dist, float* dist, float* nrm_out,
+                           float* rgb_out, cudaStream_t s);
+// read-back: stored normals -> unit xyz, stored radiance -> rgb (float32)
+cudaError_t launch_decode_normals(const void* nrm, int nrm_fmt, float* xyz, long long n, cudaStream_t s);
+cudaError_t launch_unpack_radiance(const void* rad, int rad_fmt, float* rgb, long long n, cudaStream_t s);
 
 // Read-only access to a grid for render entry points outside api.cu.
 struct GridAccess {

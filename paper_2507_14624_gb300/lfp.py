@@ -60,6 +60,11 @@ class lfp_render_opts(ctypes.Structure):
                 ("schedule", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
+class lfp_point_cloud(ctypes.Structure):
+    _fields_ = [("xyz", ctypes.c_void_p), ("rgb", ctypes.c_void_p), ("normal", ctypes.c_void_p),
+                ("n", ctypes.c_longlong), ("is_device", ctypes.c_int)]
+
+
 class LfpError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {lfp_status_string(status)} ({status})")
@@ -81,6 +86,8 @@ def _load():
         "lfp_autotune": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
         "lfp_render_backward": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, vp], i),
         "lfp_render_backward_ex": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, i, vp], i),
+        "lfp_build_probes_from_points": ([vp, i, i, P(lfp_point_cloud), ctypes.c_float, vp], i),
+        "lfp_read_probes": ([vp, i, i, vp, vp, vp, vp], i),
         "lfp_pick_levels": ([P(vp), i, P(lfp_view), i, P(ctypes.c_int32)], i),
         "lfp_render_levels": ([P(vp), i, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
         "lfp_render_backward_levels": ([P(vp), i, P(lfp_view), i, vp, vp, vp, vp, P(vp), i, vp], i),
@@ -158,6 +165,15 @@ def lfp_render_backward_ex(grid, views, n_views, grad_rgb, cls, aux_probe, aux_u
                            stream) -> None:
     _check(_lib.lfp_render_backward_ex(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance,
                                        reduction, stream), "lfp_render_backward_ex")
+
+
+def lfp_build_probes_from_points(grid, first_probe, count, cloud: lfp_point_cloud, empty_dist, stream) -> None:
+    _check(_lib.lfp_build_probes_from_points(grid, first_probe, count, ctypes.byref(cloud), empty_dist, stream),
+           "lfp_build_probes_from_points")
+
+
+def lfp_read_probes(grid, first_probe, count, dist, normal, radiance, stream) -> None:
+    _check(_lib.lfp_read_probes(grid, first_probe, count, dist, normal, radiance, stream), "lfp_read_probes")
 
 
 def _handles(grids):

@@ -89,7 +89,7 @@ def _load():
         lib.syn_probe_maps.restype = None
         lib.syn_texel_directions.argtypes = [i, vp]
         lib.syn_texel_directions.restype = None
-        lib.syn_scan.argtypes = [ctypes.POINTER(_SceneC), vp, ll, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
+        lib.syn_scan.argtypes = [ctypes.POINTER(_SceneC), vp, i, i, ctypes.c_double, ctypes.c_double, vp, vp, vp]
         lib.syn_scan.restype = None
         _lib = lib
     return _lib
@@ -592,28 +592,30 @@ def multiscale_workload(scale: int = 1, n_views: int = 64):
 
 def scan(scene: Scene, positions, n_dirs: int, seed: int, vertical_deg: float = 300.0):
     """Point cloud of one laser scan per position (Sec. 5.2: the scanner
-    sweeps 360 deg horizontally and `vertical_deg` vertically, so a cone of
-    360 - vertical_deg deg under it stays unseen). Each scan casts n_dirs
-    rays on a spherical Fibonacci lattice with a seeded azimuth phase; every
-    ray's nearest hit is a point with its radiance and surface normal.
-    Returns float32 arrays xyz [n][3], rgb [n][3], normal [n][3] (scans
-    concatenated in order)."""
+    turns 360 deg horizontally while its mirror sweeps `vertical_deg`
+    vertically, so a cone of 360 - vertical_deg deg under it stays unseen).
+    About n_dirs directions per scan on an (azimuth, polar angle) grid with
+    equal angular steps and a seeded azimuth phase, recorded column by column
+    as a scanner writes them; every ray's nearest hit is a point with its
+    radiance and surface normal. Returns float32 arrays xyz [n][3], rgb
+    [n][3], normal [n][3] (scans concatenated in order)."""
     lib = _load()
     rng = SplitMix64(seed)
-    z_min = -math.cos(math.radians((360.0 - vertical_deg) / 2.0))
+    theta_max = math.radians(vertical_deg / 2.0)
+    n_el = max(1, int(round(math.sqrt(n_dirs * theta_max / (2.0 * math.pi)))))
+    n_az = max(1, n_dirs // n_el)
     out = {"xyz": [], "rgb": [], "normal": []}
     for p in np.asarray(positions, np.float64).reshape(-1, 3):
-        xyz = np.zeros((n_dirs, 3), np.float32)
-        rgb = np.zeros((n_dirs, 3), np.float32)
-        nrm = np.zeros((n_dirs, 3), np.float32)
-        valid = np.zeros(n_dirs, np.uint8)
+        n = n_az * n_el
+        xyz = np.zeros((n, 3), np.float32)
+        rgb = np.zeros((n, 3), np.float32)
+        nrm = np.zeros((n, 3), np.float32)
         pos = np.ascontiguousarray(p)
-        lib.syn_scan(ctypes.byref(scene._cstruct()), _ptr(pos), n_dirs, rng.uniform(0.0, 2.0 * math.pi), z_min,
-                     _ptr(xyz), _ptr(rgb), _ptr(nrm), _ptr(valid))
-        keep = valid.astype(bool)
-        out["xyz"].append(xyz[keep])
-        out["rgb"].append(rgb[keep])
-        out["normal"].append(nrm[keep])
+        lib.syn_scan(ctypes.byref(scene._cstruct()), _ptr(pos), n_az, n_el, rng.uniform(0.0, 2.0 * math.pi),
+                     theta_max, _ptr(xyz), _ptr(rgb), _ptr(nrm))
+        out["xyz"].append(xyz)
+        out["rgb"].append(rgb)
+        out["normal"].append(nrm)
     return {k: np.ascontiguousarray(np.concatenate(v)) for k, v in out.items()}
 
 

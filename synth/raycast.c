@@ -299,29 +299,30 @@ void syn_probe_maps(const syn_scene* sc, int P, const double* probe_pos, int N,
     }
 }
 
-/* A laser-scanner sweep from one position: n_dirs directions on a spherical
- * Fibonacci lattice (direction k: z = 1 - (2k + 1) / n_dirs, azimuth
- * phase + k * pi (3 - sqrt 5)), the ones with z < z_min (the cone the
- * scanner's tripod hides) marked invalid. Each valid ray's nearest hit gives
- * a point, its radiance and its surface normal (float32). */
-void syn_scan(const syn_scene* sc, const double* pos, long long n_dirs, double phase, double z_min,
-              float* xyz, float* rgb, float* nrm, unsigned char* valid) {
-    const double golden = 3.14159265358979323846 * (3.0 - sqrt(5.0));
+/* A laser-scanner sweep from one position, in the order a scanner records
+ * it: n_az azimuth columns (azimuth phase + 2 pi (a + 1/2) / n_az), each a
+ * vertical sweep of n_el directions with polar angle theta_max (e + 1/2) /
+ * n_el from the zenith (theta_max = 150 deg for a 300 deg vertical field:
+ * the cone under the tripod stays unseen). Point k = a n_el + e is the
+ * nearest hit of that direction, with its radiance and surface normal
+ * (float32). */
+void syn_scan(const syn_scene* sc, const double* pos, int n_az, int n_el, double phase, double theta_max,
+              float* xyz, float* rgb, float* nrm) {
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    const long long n = (long long)n_az * n_el;
 #pragma omp parallel for schedule(dynamic, 1024)
-    for (long long k = 0; k < n_dirs; ++k) {
-        double z = 1.0 - (2.0 * (double)k + 1.0) / (double)n_dirs;
-        double r = sqrt(fmax(0.0, 1.0 - z * z));
-        double phi = phase + (double)k * golden;
-        double d[3] = {r * cos(phi), r * sin(phi), z};
-        valid[k] = z >= z_min;
-        if (!valid[k]) continue;
+    for (long long k = 0; k < n; ++k) {
+        int a = (int)(k / n_el), e = (int)(k % n_el);
+        double phi = phase + two_pi * (a + 0.5) / n_az;
+        double th = theta_max * (e + 0.5) / n_el;
+        double d[3] = {sin(th) * cos(phi), sin(th) * sin(phi), cos(th)};
         double t, nn[3], c[3];
         int prim;
         cast_one(sc, pos, d, &t, nn, c, &prim);
-        for (int a = 0; a < 3; ++a) {
-            xyz[3 * k + a] = (float)(pos[a] + t * d[a]);
-            rgb[3 * k + a] = (float)c[a];
-            nrm[3 * k + a] = (float)nn[a];
+        for (int q = 0; q < 3; ++q) {
+            xyz[3 * k + q] = (float)(pos[q] + t * d[q]);
+            rgb[3 * k + q] = (float)c[q];
+            nrm[3 * k + q] = (float)nn[q];
         }
     }
 }

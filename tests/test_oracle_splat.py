@@ -72,11 +72,12 @@ def test_brute_force_nearest_point_per_texel_with_ties():
             q = f(f(v[0] * v[0]) + f(v[1] * v[1]))
             q = f(q + f(v[2] * v[2]))
             s = f(f(abs(v[0]) + abs(v[1])) + abs(v[2]))
-            px, py = f(v[0] / s), f(v[1] / s)
+            inv = f(f(1) / s)
+            px, py = f(v[0] * inv), f(v[1] * inv)
             if v[2] < 0:
                 px, py = (f((f(1) - abs(py)) * (1 if px >= 0 else -1)), f((f(1) - abs(px)) * (1 if py >= 0 else -1)))
-            i = min(int(np.floor(f((px + f(1)) * f(N / 2)))), N - 1)
-            j = min(int(np.floor(f((py + f(1)) * f(N / 2)))), N - 1)
+            i = min(max(int(np.floor(f((px + f(1)) * f(N / 2)))), 0), N - 1)
+            j = min(max(int(np.floor(f((py + f(1)) * f(N / 2)))), 0), N - 1)
             if (j, i) not in best or (q, k) < best[(j, i)]:
                 best[(j, i)] = (q, k)
         for j in range(N):
