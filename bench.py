@@ -14,7 +14,7 @@ the host cores (cpu_baseline), fwd+adjoint ms/view on the differentiable-fit
 views, and SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lfp|reference]
-                  [--workload room|batched|fit|few|multiscale|build]
+                  [--workload room|batched|fit|few|multiscale|build|sweep]
 (few: four probes, the nearest-probe traversal Sec. 4.3 gives for fewer than
 8 probes, on the loop-nest kernel.)
 Under torchrun every rank renders its own copy of the workload (weak scaling,
@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lfp", choices=["lfp", "reference"])
-    ap.add_argument("--workload", default="room", choices=["room", "batched", "fit", "few", "multiscale", "build"])
+    ap.add_argument("--workload", default="room",
+                    choices=["room", "batched", "fit", "few", "multiscale", "build", "sweep"])
     ap.add_argument("--views", type=int, default=64, help="multiscale: number of views (64 in the configuration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -382,6 +383,10 @@ def run_reference(args):
         return run_reference_multiscale(args)
     if args.workload == "build":
         return run_reference_build(args)
+    if args.workload == "sweep":
+        print(json.dumps({"impl": "reference", "unavailable": "the resolution sweep is a study over probe "
+                          "settings, not a throughput workload; the oracle arms of room and build cover it"}))
+        return
     sc, views, d, n, r = build_workload(args.workload)
     o = oracle.Oracle(sc.grid, d, n, r, traversal=1 if args.workload == "few" else 0)
     v = views[0]
@@ -750,6 +755,96 @@ def run_build(args):
         torch.distributed.destroy_process_group()
 
 
+def pinhole_rays(v):
+    """Float64 camera rays of a view (pinhole of lfp_view), for the analytic truth."""
+    import numpy as np
+    xs, ys = np.meshgrid(np.arange(v.W), np.arange(v.H))
+    xs, ys = xs.ravel(), ys.ravel()
+    th = np.tan(v.fov_y / 2)
+    a = ((xs + 0.5) / v.W * 2 - 1) * th * v.W / v.H
+    b = (1 - (ys + 0.5) / v.H * 2) * th
+    D = np.array(v.fwd)[None] + a[:, None] * np.array(v.right)[None] + b[:, None] * np.array(v.up)[None]
+    D /= np.linalg.norm(D, axis=1, keepdims=True)
+    return np.repeat(np.array(v.pos, np.float64)[None], len(D), 0), D
+
+
+def run_sweep(args):
+    """Resolution sweep (the Sec. 6 study of map resolutions): the room scene
+    and its 1080p view, full-resolution maps N in {1024, 2048, 3072} and
+    low-resolution maps M in {64, 128}, probes either ray-cast (one ray per
+    texel centre) or built on the GPU from a fixed point cloud (4 scans of
+    28 M directions, the paper's capture size). Per setting: image error
+    against the analytic scene and ms per frame."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2507_14624_gb300 as lfpk
+    torch.cuda.set_device(dist_env()[2])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sc, views = synth.workload("room")
+    v = views[0]
+    X, D = pinhole_rays(v)
+    _, _, truth, _ = sc.cast(X, D)
+    pc = synth.scan(sc, synth.scan_positions(sc, 4, 2024), 28_000_000, seed=2025)
+    xyz, rgb = (torch.tensor(pc[k], device=dev) for k in ("xyz", "rgb"))
+    n_pts = len(pc["xyz"])
+    del pc
+    rows, e = [], None
+    for N in (1024, 2048, 3072):
+        for source in ("scan", "raycast"):
+            grids = {M: lfpk.ProbeGrid(synth.Grid(4, 4, 4, 0.5, N, M)) for M in (64, 128)}
+            if source == "scan":
+                for g in grids.values():
+                    g.build_from_points(xyz, rgb, empty_dist=0.0)
+                empty = float((grids[64].read_probes()[0] == 0).float().mean().item())
+            else:
+                P = sc.grid.probe_positions()
+                for p0 in range(0, len(P), 4):
+                    d, n, r = sc.probe_maps(P[p0:p0 + 4], N=N)
+                    for g in grids.values():
+                        g.upload(d, n, r, first_probe=p0)
+                empty = 0.0
+            images = {}
+            for M, g in grids.items():
+                out = g.render([v])
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(5):
+                    g.render([v], aux=False)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 5
+                cls = out["cls"].cpu().numpy()
+                img = out["rgb"].cpu().numpy().astype(np.float64)
+                images[M] = (cls, img)
+                hit = cls == 1
+                err = np.abs(img - truth).max(1)
+                rows.append({"N": N, "M": M, "probes": source, "ms_per_frame": round(ms, 4),
+                             "mrays_per_s": round(v.W * v.H / ms / 1e3, 1), "hit": round(float(hit.mean()), 5),
+                             "within_0.02": round(float((hit & (err < 0.02)).mean()), 4),
+                             "within_0.05": round(float((hit & (err < 0.05)).mean()), 4),
+                             "mean_abs_err_hit": round(float(np.abs(img - truth)[hit].mean()), 5),
+                             "empty_texels": round(empty, 5)})
+            # the min/max map only skips work: the two M give the same image up
+            # to FP32 near-ties at coarse-texel entries
+            differ = (images[64][0] != images[128][0]) | (np.abs(images[64][1] - images[128][1]).max(1) > 1e-5)
+            for r in rows[-2:]:
+                r["pixels_differing_between_M"] = round(float(differ.mean()), 7)
+            for g in grids.values():
+                g.close()
+            torch.cuda.empty_cache()
+    ref = next(r for r in rows if r["N"] == 2048 and r["M"] == 128 and r["probes"] == "scan")
+    line = {"metric": "resolution sweep: Mrays/s at 1080p and error vs the analytic scene per (N, M, probe source)",
+            "value": ref["mrays_per_s"], "unit": "Mrays/s", "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32", "data": "synthetic (seeded room scene; ray-cast probes and simulated laser scans)",
+            "config": {"workload": "sweep: room grid 4x4x4 spacing 0.5, 1 view 1920x1080; N in 1024/2048/3072, "
+                                   "M in 64/128; probes ray-cast or splatted from 4 scans of 28 M directions",
+                       "points": n_pts, "value_is": "N=2048, M=128, splatted probes (the paper's room setting)"},
+            "sweep": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_fit(args):
     """Differentiable fit: the room grid (seed 4), 64 views of 800x800, targets
     = ground-truth render + N(0, 0.01^2); radiance re-initialised U[0,1]; L2
@@ -784,6 +879,8 @@ if __name__ == "__main__":
         run_multiscale(a)
     elif a.workload == "build" and a.impl != "reference":
         run_build(a)
+    elif a.workload == "sweep" and a.impl != "reference":
+        run_sweep(a)
     elif a.impl == "reference":
         run_reference(a)
     else:
