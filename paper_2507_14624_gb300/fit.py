@@ -5,6 +5,11 @@ adjoint kernel (lfp_render_backward_ex), joined by the torch.autograd.Function
 in this package; the optimiser is torch's fused Adam over the radiance
 tensor. Distance and normal maps stay fixed, so the loss is quadratic in
 radiance and Adam converges to the noise floor of the targets.
+
+Data parallel: with a process group of W ranks, rank r renders views r, r+W,
+... and scatters its pixels' gradients locally; one all-reduce (sum) of the
+radiance gradient per step then gives every rank the gradient of the whole
+loss, and the replicated Adam steps stay identical.
 """
 from __future__ import annotations
 
@@ -24,26 +29,56 @@ def make_targets(grid: ProbeGrid, views, sigma: float = 0.01, seed: int = 404):
     return clean + noise
 
 
+def shard_views(views, rank: int, world: int):
+    """The views rank `rank` of `world` renders: every world-th, from `rank`."""
+    return list(views)[rank::world]
+
+
+def shard_pixels(views, rank: int, world: int):
+    """Flat pixel index ranges ([begin, end) into the concatenated views) of
+    the rank's views, in its rendering order."""
+    offs, o = [], 0
+    for v in views:
+        offs.append((o, o + v.W * v.H))
+        o += v.W * v.H
+    return offs[rank::world]
+
+
+def allreduce_gradient(grad, group=None):
+    """Sum a gradient over the ranks of `group` (no-op without one)."""
+    import torch.distributed as dist
+    if group is not None or (dist.is_available() and dist.is_initialized()):
+        if dist.get_world_size(group) > 1:
+            dist.all_reduce(grad, op=dist.ReduceOp.SUM, group=group)
+    return grad
+
+
 def fit_radiance(grid: ProbeGrid, views, targets, steps: int = 200, lr: float = 1e-2, seed: int = 404,
-                 init=None, log_every: int = 0):
+                 init=None, log_every: int = 0, group=None, total_pixels=None):
     """Fit radiance [P][N][N][3] (re-initialised U[0,1] unless `init` is given)
-    to `targets` [pixels][3] with an L2 loss. Returns (radiance, history) where
-    history holds (step, mse, ms) tuples of the logged steps and the last one."""
+    to `targets` [pixels][3] with an L2 loss (the mean over all ranks' pixels
+    and channels). With a process group, `views` / `targets` are this rank's
+    shard (shard_views / shard_pixels) and `total_pixels` the pixels of all
+    ranks. Returns (radiance, history) where history holds (step, mse, ms)
+    tuples of the logged steps and the last one (mse of this rank's shard)."""
     P, N = grid.n_probes, grid.N
     if init is None:
         gen = torch.Generator(device="cuda").manual_seed(seed)
         init = torch.rand((P, N, N, 3), device="cuda", generator=gen)
     rad = init.clone().requires_grad_(True)
     opt = torch.optim.Adam([rad], lr=lr, fused=True)
+    denom = 3.0 * (targets.shape[0] if total_pixels is None else total_pixels)
     history = []
     t0 = time.perf_counter()
     for it in range(steps):
         opt.zero_grad(set_to_none=False)
         rgb, _ = render(rad, grid, views)
-        loss = ((rgb - targets) ** 2).mean()
+        loss = ((rgb - targets) ** 2).sum() / denom
         loss.backward()
+        allreduce_gradient(rad.grad, group)
         opt.step()
         if (log_every and it % log_every == 0) or it == steps - 1:
             torch.cuda.synchronize()
-            history.append((it, loss.item(), (time.perf_counter() - t0) * 1e3 / (it + 1)))
+            mse = ((rgb.detach() - targets) ** 2).mean().item()
+            history.append((it, mse, (time.perf_counter() - t0) * 1e3 / (it + 1)))
     return rad.detach(), history
