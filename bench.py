@@ -308,6 +308,9 @@ def run_lfp(args):
     extra = {}
     if not args.no_adjoint and rank == 0:
         extra["fwd_adj_ms_per_view"] = fwd_adjoint_ms_per_view(torch, lfpk, dev)
+    if f16 and rank == 0:
+        extra["vs_single_view_fp32"] = single_view_fp32(torch, lfpk, lfp, sc, views, d, n, r, cls, flush,
+                                                        value, args.steps)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(sc, views, d, n, r, budget_s=10.0, traversal=int(trav))
@@ -324,6 +327,52 @@ def run_lfp(args):
     grid.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def single_view_fp32(torch, lfpk, lfp, sc, views, d, n, r, cls_f16, flush, batched_value, steps):
+    """The same views as the plain form: FP32 texels, one launch per view
+    (each view its own lfp_render_ex call), L2 flushed before each step; plus
+    the class agreement of the FP16 batched images with the FP32 ones."""
+    g = lfpk.ProbeGrid(sc.grid)
+    g.upload(d, n, r)
+    dev = cls_f16.device
+    total = sum(v.W * v.H for v in views)
+    rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
+    cls = torch.empty(total, dtype=torch.uint8, device=dev)
+    singles = []
+    off = 0
+    for v in views:
+        arr, nv, _ = lfpk.make_views([v])
+        arr[0].out_offset = off
+        singles.append(arr)
+        off += v.W * v.H
+    o = lfp.lfp_outputs()
+    o.rgb, o.cls = rgb.data_ptr(), cls.data_ptr()
+    sh = lfpk._stream_handle()
+
+    def step():
+        for arr in singles:
+            lfp.lfp_render_ex(g.handle, arr, 1, o, None, sh)
+
+    flush.fill_(1.0)
+    step()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    ms /= steps
+    agree = float((cls == cls_f16).float().mean().item())
+    g.close()
+    plain = total / ms / 1e3
+    return {"plain_fp32_single_view_mrays_per_s": round(plain, 3), "ms_per_step": round(ms, 4),
+            "launches_per_step": len(views), "batched_fp16_speedup": round(batched_value / plain, 4),
+            "class_agreement_fp16_vs_fp32": round(agree, 7)}
 
 
 def fwd_adjoint_ms_per_view(torch, lfpk, dev, steps=5):

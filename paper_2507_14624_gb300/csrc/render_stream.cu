@@ -561,11 +561,12 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
         // ---- walk phase: one texel visit per walking lane per step, until
         // kBatchPct % of the busy lanes wait for a transition ----
         const int busy = __popc(__ballot_sync(kFull, L.mode != kIdle && L.mode != kExit));
+        const int need = (kBatchPct * busy + 99) / 100;  // waiting lanes that end the phase
 #pragma unroll 1
         for (int r = 0; r < kWalkSteps; ++r) {
             if (L.mode == kWalk) walk_step<NRMF, COUNT>(g, L, st);
             const int walking = __popc(__ballot_sync(kFull, L.mode == kWalk));
-            if (100 * (busy - walking) >= kBatchPct * busy) break;
+            if (busy - walking >= need) break;
         }
     }
     if (COUNT) {
