@@ -7,7 +7,8 @@
 // a warp waits for its slowest ray. Here every loop iteration gives each lane
 // one texel visit at whichever level it is on (the low- and full-resolution
 // visits are the same instructions with different operands); the rare
-// transitions (next segment, probe, cell, ray) run in a side branch, and a
+// transitions (a full-resolution crossing's decision, next segment, probe,
+// cell, ray) run in a side branch, and a
 // lane whose ray is done takes the next ray from its warp's pool of 8x4 ray
 // tiles, refilled from a global queue. Results are identical to the nested
 // engine: the same arithmetic decides every texel.
@@ -46,7 +47,8 @@ enum Mode : int {
     kUnknownRes,   // the probe returned UNKNOWN
     kNextCell,     // the probe returned MISS, or all 8 were UNKNOWN
     kRayDone,      // write the pixel
-    kExit          // no rays left
+    kExit,         // no rays left
+    kDecide        // full-resolution crossing: normal test and hit point
 };
 
 // Per-lane state. The walk's working set lives in registers (Lane); the
@@ -72,6 +74,7 @@ enum ColdF {
     // segment fields used only when a walk descends, decides or ascends
     kW0, kW1, kW2, kYa0, kYa1, kYa2, kCp, kTstar, kP00, kP01, kK0, kK1, kUend,
     kUxc, kUyc, kUec,  // the low-resolution texel being refined: next crossings, exit
+                       // (at a pending decision kUxc, kUyc hold the texel value and exit u)
     kNumColdF
 };
 enum ColdI { kC0, kC1, kC2, kCbits, kOrder, kQ, kKq, kSegI, kSegFinal, kCls, kQuad, kI, kJ, kLastc, kNumColdI };
@@ -170,9 +173,10 @@ __device__ __forceinline__ void probe_start(const GridDev& g, Lane& L) {
     float cx = w.x != 0.0f ? (O.x - X.x) * __frcp_rn(w.x) : kInf;
     float cy = w.y != 0.0f ? (O.y - X.y) * __frcp_rn(w.y) : kInf;
     float cz = w.z != 0.0f ? (O.z - X.z) * __frcp_rn(w.z) : kInf;
-    cx = (cx > t0 && cx < t1) ? cx : kInf;
-    cy = (cy > t0 && cy < t1) ? cy : kInf;
-    cz = (cz > t0 && cz < t1) ? cz : kInf;
+    const float t_far = t0 + kFarCuts * g.spacing;  // as in trace_probe
+    cx = (cx > t0 && cx < t1 && cx < t_far) ? cx : kInf;
+    cy = (cy > t0 && cy < t1 && cy < t_far) ? cy : kInf;
+    cz = (cz > t0 && cz < t1 && cz < t_far) ? cz : kInf;
     CF(kCut0) = fminf(cx, fminf(cy, cz));
     CF(kCut2) = fmaxf(cx, fmaxf(cy, cz));
     CF(kCut1) = fmaxf(fminf(cx, cy), fminf(fmaxf(cx, cy), cz));
@@ -252,16 +256,20 @@ __device__ __forceinline__ float lane_r2(float tau) {
 }
 
 // Advance past the current texel (exit ue) over the earlier next boundary;
-// false when the walk leaves the current level's index box.
+// false when the walk leaves the current level's index box. The axis is
+// selected into shared operands so both cases run the same instructions.
 __device__ __forceinline__ bool advance(Lane& L, int scale, float ue, float Pb, float D2b) {
-    if (L.ux <= L.uy) {
-        L.i += L.dir0;
-        if (L.i < L.lo0 || L.i > L.hi0) return false;
-        L.ux = fmaxf(fmaf((float)((L.dir0 > 0 ? L.i + 1 : L.i) * scale), L.m0, L.q0), ue);
+    const bool xs = L.ux <= L.uy;
+    const int dir = xs ? L.dir0 : L.dir1;
+    const int c = (xs ? L.i : L.j) + dir;
+    if (c < (xs ? L.lo0 : L.lo1) || c > (xs ? L.hi0 : L.hi1)) return false;
+    const float un = fmaxf(fmaf((float)((dir > 0 ? c + 1 : c) * scale), xs ? L.m0 : L.m1, xs ? L.q0 : L.q1), ue);
+    if (xs) {
+        L.i = c;
+        L.ux = un;
     } else {
-        L.j += L.dir1;
-        if (L.j < L.lo1 || L.j > L.hi1) return false;
-        L.uy = fmaxf(fmaf((float)((L.dir1 > 0 ? L.j + 1 : L.j) * scale), L.m1, L.q1), ue);
+        L.j = c;
+        L.uy = un;
     }
     L.u = ue;
     L.Pa = Pb;
@@ -305,11 +313,13 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
         vmax = mm.y;
         if (COUNT) st.coarse++;
     }
-    st.steps++;
-    if (g.max_steps > 0 && (int)st.steps >= g.max_steps) {
-        CI(kCls) = kStepLimit;
-        L.mode = kRayDone;
-        return;
+    if (COUNT) {  // the instrumented kernel also enforces the max_steps cap
+        st.steps++;
+        if (g.max_steps > 0 && (int)st.steps >= g.max_steps) {
+            CI(kCls) = kStepLimit;
+            L.mode = kRayDone;
+            return;
+        }
     }
     float d2 = v * v;
     if (L.Pa < d2 * L.D2a && Pb < d2 * D2b) {  // the ray stays in front of the stored surface
@@ -345,7 +355,19 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
         L.uy = L.dir1 == 0 ? kInf : fmaxf(fmaf((float)(L.dir1 > 0 ? L.j + 1 : L.j), L.m1, L.q1), L.u);
         return;
     }
-    // full-resolution crossing: the normal decides (highResolutionTracing)
+    // full-resolution crossing: decided in the control round (kDecide), which
+    // keeps the walk loop's code small
+    CF(kUxc) = v;
+    CF(kUyc) = ue;
+    L.mode = kDecide;
+}
+
+// The normal decides a full-resolution crossing (highResolutionTracing):
+// HIT with its shading uv, else UNKNOWN.
+template <int NRMF, bool COUNT>
+__device__ __forceinline__ void decide(const GridDev& g, Lane& L, Stats<COUNT>& st) {
+    const int N = g.N;
+    const float v = CF(kUxc), ue = CF(kUyc);
     float ta = lane_tau(L, L.u), tb = lane_tau(L, ue);
     float d = v, dk = d * g.kappa;
     L.mode = kUnknownRes;
@@ -448,7 +470,9 @@ __device__ __forceinline__ void write_ray(const GridDev& g, const OutDev& out, c
 }
 
 // Persistent kernel: every warp pulls 8x4 ray tiles from `queue` and keeps
-// its 32 lanes busy, one texel visit per lane per iteration.
+// its 32 lanes busy, one texel visit per lane per iteration. COUNT selects
+// the instrumented variant (fetch counters and the max_steps cap); the plain
+// variant carries neither, which keeps the per-visit path short.
 template <int RADF, int NRMF, bool COUNT>
 __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_stream_kernel(GridDev g, ViewBatch vb, OutDev out,
                                                                           unsigned* queue) {
@@ -466,6 +490,7 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
     for (;;) {
         // ---- control round: every transition runs once, in pipeline order,
         // for all lanes that need it, so lanes reconverge at each stage ----
+        if (L.mode == kDecide) decide<NRMF, COUNT>(g, L, st);
         if (L.mode == kRayDone) {
             write_ray<RADF>(g, out, L);
             if (COUNT) {
@@ -569,7 +594,7 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
             if (busy - walking >= need) break;
         }
     }
-    if (COUNT) {
+    if (COUNT && out.counters) {
         for (int q = 0; q < kNumCounters; ++q) {
             unsigned long long v = acc[q];
             for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
@@ -581,7 +606,7 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
 template <int RADF, int NRMF>
 cudaError_t launch_stream_fmt(const GridDev& g, const ViewBatch& vb, const OutDev& out, unsigned* queue, int blocks,
                               cudaStream_t s) {
-    if (out.counters)
+    if (out.counters || g.max_steps > 0)
         render_stream_kernel<RADF, NRMF, true><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
     else
         render_stream_kernel<RADF, NRMF, false><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);

@@ -26,6 +26,7 @@ namespace lfp {
 namespace trace {
 
 constexpr float kInf = __builtin_huge_valf();
+constexpr float kFarCuts = 1048576.0f;  // 2^20 grid spacings: octant cuts beyond are dropped
 
 struct Ray {
     float3 X, w;
@@ -331,9 +332,13 @@ __device__ void trace_probe(const GridDev& g, const Ray& r, int probe, float3 O,
     float cx = r.w.x != 0.0f ? (O.x - r.X.x) * __frcp_rn(r.w.x) : kInf;
     float cy = r.w.y != 0.0f ? (O.y - r.X.y) * __frcp_rn(r.w.y) : kInf;
     float cz = r.w.z != 0.0f ? (O.z - r.X.z) * __frcp_rn(r.w.z) : kInf;
-    cx = (cx > t0 && cx < t1) ? cx : kInf;
-    cy = (cy > t0 && cy < t1) ? cy : kInf;
-    cz = (cz > t0 && cz < t1) ? cz : kInf;
+    // a cut further than kFarCuts spacings belongs to a ray almost parallel
+    // to that probe plane: no closed scene decides anything that far out, and
+    // a segment that long would lose the float32 resolution of its near end
+    const float t_far = t0 + kFarCuts * g.spacing;
+    cx = (cx > t0 && cx < t1 && cx < t_far) ? cx : kInf;
+    cy = (cy > t0 && cy < t1 && cy < t_far) ? cy : kInf;
+    cz = (cz > t0 && cz < t1 && cz < t_far) ? cz : kInf;
     float c0 = fminf(cx, fminf(cy, cz)), c2 = fmaxf(cx, fmaxf(cy, cz));
     float c1 = fmaxf(fminf(cx, cy), fminf(fmaxf(cx, cy), cz));  // median
     out.cls = kMiss;
