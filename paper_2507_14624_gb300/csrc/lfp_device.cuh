@@ -76,12 +76,20 @@ struct OutDev {
 };
 
 __device__ __forceinline__ float sgn_nz(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
+// Fast division and reciprocal (about 2 ulp, no special-case code path) for
+// the per-ray, per-cell and per-probe set-up: short code matters more than
+// the last bit there. Two places keep correctly rounded arithmetic: the
+// segment set-up (its reciprocals place every texel-boundary crossing) and
+// camera-ray generation. Cell faces and octant cuts use the same frcp, so a
+// face through a probe is never a cut.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float frcp(float b) { return __fdividef(1.0f, b); }
 
 // Octahedral map (Sec. 3): direction -> octahedron -> square, lower octants
 // folded onto the corners (the unfold of Cigolle et al., JCGT 2014).
 __device__ __forceinline__ float2 oct_encode(float x, float y, float z) {
     float l1 = fabsf(x) + fabsf(y) + fabsf(z);
-    float px = x / l1, py = y / l1;
+    float px = fdiv(x, l1), py = fdiv(y, l1);
     if (z < 0.0f) {
         float fx = (1.0f - fabsf(py)) * sgn_nz(px);
         float fy = (1.0f - fabsf(px)) * sgn_nz(py);

@@ -108,7 +108,7 @@ __device__ __forceinline__ bool ray_enter_grid(const GridDev& g, float3 X, float
             if (Xa[a] < lo || Xa[a] > hi) t_enter = kInf;
             continue;
         }
-        float ta = (lo - Xa[a]) / Wa[a], tb = (hi - Xa[a]) / Wa[a];
+        float ta = fdiv(lo - Xa[a], Wa[a]), tb = fdiv(hi - Xa[a], Wa[a]);
         if (ta > tb) { float x = ta; ta = tb; tb = x; }
         t_enter = fmaxf(t_enter, ta);
         t_exit = fminf(t_exit, tb);
@@ -118,7 +118,7 @@ __device__ __forceinline__ bool ray_enter_grid(const GridDev& g, float3 X, float
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float p = fmaf(t_enter, Wa[a], Xa[a]);
-        c[a] = min(max((int)floorf((p - og[a]) / g.spacing), 0), nc[a] - 1);
+        c[a] = min(max((int)floorf(fdiv(p - og[a], g.spacing)), 0), nc[a] - 1);
         bits |= (Wa[a] > 0.0f ? 1 : (Wa[a] < 0.0f ? 2 : 0)) << (2 * a);
     }
     CI(kC0) = c[0];
@@ -142,7 +142,7 @@ __device__ __forceinline__ void cell_start(const GridDev& g) {
     for (int a = 0; a < 3; ++a) {
         int st = step_of(cbits, a);
         tm[a] = st == 0 ? kInf
-                        : (grid_plane(og[a], g.spacing, c[a] + (st > 0 ? 1 : 0)) - Xa[a]) * __frcp_rn(Wa[a]);
+                        : (grid_plane(og[a], g.spacing, c[a] + (st > 0 ? 1 : 0)) - Xa[a]) * frcp(Wa[a]);
     }
     int ax = 0;
     if (tm[1] < tm[ax]) ax = 1;
@@ -170,9 +170,9 @@ __device__ __forceinline__ void probe_start(const GridDev& g, Lane& L) {
     float3 O = corner_pos(g, c0, c1, c2, kq);
     const float3 X = ray_X(), w = ray_w();
     const float t0 = CF(kTin), t1 = CF(kTout);
-    float cx = w.x != 0.0f ? (O.x - X.x) * __frcp_rn(w.x) : kInf;
-    float cy = w.y != 0.0f ? (O.y - X.y) * __frcp_rn(w.y) : kInf;
-    float cz = w.z != 0.0f ? (O.z - X.z) * __frcp_rn(w.z) : kInf;
+    float cx = w.x != 0.0f ? (O.x - X.x) * frcp(w.x) : kInf;
+    float cy = w.y != 0.0f ? (O.y - X.y) * frcp(w.y) : kInf;
+    float cz = w.z != 0.0f ? (O.z - X.z) * frcp(w.z) : kInf;
     const float t_far = t0 + kFarCuts * g.spacing;  // as in trace_probe
     cx = (cx > t0 && cx < t1 && cx < t_far) ? cx : kInf;
     cy = (cy > t0 && cy < t1 && cy < t_far) ? cy : kInf;
@@ -243,10 +243,11 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     L.uy = L.dir1 == 0 ? kInf : fmaxf(fmaf((float)((L.dir1 > 0 ? L.j + 1 : L.j) * k), L.m1, L.q1), 0.0f);
 }
 
-// tau from the segment start of walk parameter u (infinite past the end)
+// tau from the segment start of walk parameter u (infinite past the end),
+// the same arithmetic as tau_of
 __device__ __forceinline__ float lane_tau(const Lane& L, float u) {
     float D = fmaf(-L.e, u, 1.0f);
-    return D > 0.0f ? CF(kCp) * u / D : kInf;
+    return D > 0.0f ? __fdividef(CF(kCp) * u, D) : kInf;
 }
 
 __device__ __forceinline__ float lane_r2(float tau) {
@@ -425,7 +426,7 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
     const float og[3] = {g.ox, g.oy, g.oz}, Xa[3] = {X.x, X.y, X.z};
     int iv[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) iv[q] = min(max((int)rintf((Xa[q] - og[q]) / g.spacing), 0), nc[q]);
+    for (int q = 0; q < 3; ++q) iv[q] = min(max((int)rintf(fdiv(Xa[q] - og[q], g.spacing)), 0), nc[q]);
     int p = iv[0] + g.nx * (iv[1] + g.ny * iv[2]);
     float3 O = corner_pos(g, iv[0], iv[1], iv[2], 0);
     float ex = X.x - O.x, ey = X.y - O.y, ez = X.z - O.z;

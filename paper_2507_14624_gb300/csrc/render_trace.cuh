@@ -118,9 +118,12 @@ __device__ __forceinline__ float next_cross(const Seg& s, int a, int i, float u_
     return fmaxf(fmaf((float)b, s.m[a], s.q[a]), u_now);
 }
 
+// tau of walk parameter u (infinite past the end). D is in (0, 1], so the
+// fast division (2 ulp, no special-case path) is exact enough and keeps the
+// walk loop's code short.
 __device__ __forceinline__ float tau_of(const Seg& s, float u) {
     float D = fmaf(-s.e, u, 1.0f);
-    return D > 0.0f ? s.cp * u / D : kInf;
+    return D > 0.0f ? __fdividef(s.cp * u, D) : kInf;
 }
 
 __device__ __forceinline__ float r2_tau(const Seg& s, float tau) {
@@ -141,12 +144,12 @@ __device__ __forceinline__ float hit_time(const Seg& s, float ta, float tb, floa
     float sq = sqrtf(fmaxf(B * B - A * C, 0.0f));
     float t;
     if (r2_tau(s, ta) < d * d) {
-        t = B > 0.0f ? -C / (B + sq) : (sq - B) / A;  // larger root
+        t = B > 0.0f ? fdiv(-C, B + sq) : fdiv(sq - B, A);  // larger root
     } else {
-        float tstar = -B / A;
+        float tstar = fdiv(-B, A);
         if (!(tstar > ta)) return ta;
         if (B * B - A * C < 0.0f) t = tstar;
-        else t = B < 0.0f ? C / (sq - B) : -(B + sq) / A;  // smaller root
+        else t = B < 0.0f ? fdiv(C, sq - B) : fdiv(-(B + sq), A);  // smaller root
     }
     return fminf(fmaxf(t, ta), tb);
 }
@@ -329,9 +332,9 @@ __device__ void trace_probe(const GridDev& g, const Ray& r, int probe, float3 O,
     // cut points strictly inside (t0, t1), sorted: c0 <= c1 <= c2 (inf = none);
     // the same expression as the cell faces, so a face through the probe is
     // never a cut
-    float cx = r.w.x != 0.0f ? (O.x - r.X.x) * __frcp_rn(r.w.x) : kInf;
-    float cy = r.w.y != 0.0f ? (O.y - r.X.y) * __frcp_rn(r.w.y) : kInf;
-    float cz = r.w.z != 0.0f ? (O.z - r.X.z) * __frcp_rn(r.w.z) : kInf;
+    float cx = r.w.x != 0.0f ? (O.x - r.X.x) * frcp(r.w.x) : kInf;
+    float cy = r.w.y != 0.0f ? (O.y - r.X.y) * frcp(r.w.y) : kInf;
+    float cz = r.w.z != 0.0f ? (O.z - r.X.z) * frcp(r.w.z) : kInf;
     // a cut further than kFarCuts spacings belongs to a ray almost parallel
     // to that probe plane: no closed scene decides anything that far out, and
     // a segment that long would lose the float32 resolution of its near end
@@ -397,7 +400,7 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
     {
         int iv[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) iv[a] = min(max((int)rintf((Xa[a] - og[a]) / g.spacing), 0), nc[a]);
+        for (int a = 0; a < 3; ++a) iv[a] = min(max((int)rintf(fdiv(Xa[a] - og[a], g.spacing)), 0), nc[a]);
         int p = iv[0] + g.nx * (iv[1] + g.ny * iv[2]);
         float3 O = probe_pos(g, p);
         float dx = Xa[0] - O.x, dy = Xa[1] - O.y, dz = Xa[2] - O.z;
@@ -476,7 +479,7 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
             if (Xa[a] < lo || Xa[a] > hi) t_enter = kInf;
             continue;
         }
-        float ta = (lo - Xa[a]) / Wa[a], tb = (hi - Xa[a]) / Wa[a];
+        float ta = fdiv(lo - Xa[a], Wa[a]), tb = fdiv(hi - Xa[a], Wa[a]);
         if (ta > tb) { float x = ta; ta = tb; tb = x; }
         t_enter = fmaxf(t_enter, ta);
         t_exit = fminf(t_exit, tb);
@@ -486,7 +489,7 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float p = fmaf(t_enter, Wa[a], Xa[a]);
-        c[a] = min(max((int)floorf((p - og[a]) / g.spacing), 0), nc[a] - 1);
+        c[a] = min(max((int)floorf(fdiv(p - og[a], g.spacing)), 0), nc[a] - 1);
         step[a] = Wa[a] > 0.0f ? 1 : (Wa[a] < 0.0f ? -1 : 0);
     }
     bool saw_unknown = false, step_limited = false;
@@ -497,7 +500,7 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
         for (int a = 0; a < 3; ++a)
             tm[a] = step[a] == 0 ? kInf
                                  : (grid_plane(og[a], g.spacing, c[a] + (step[a] > 0 ? 1 : 0)) - Xa[a]) *
-                                       __frcp_rn(Wa[a]);
+                                       frcp(Wa[a]);
         int ax = 0;
         if (tm[1] < tm[ax]) ax = 1;
         if (tm[2] < tm[ax]) ax = 2;
