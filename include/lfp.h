@@ -208,6 +208,18 @@ lfp_status lfp_autotune(lfp_grid* grid, const lfp_view* views, int n_views,
 lfp_status lfp_render_to_host(lfp_grid* grid, const lfp_view* views, int n_views,
                               float* rgb_host, uint8_t* cls_host, void* cuda_stream);
 
+/* Frame-loop form of lfp_render_to_host: renders on `cuda_stream` into one
+ * of two grid-owned device buffers (used in turn) and queues the copy of
+ * rgb / cls to the host buffers on a grid-owned copy stream, then returns
+ * without waiting, so the copy of one call overlaps the render of the next.
+ * Copies run in call order. The host buffers of a call hold its result
+ * once lfp_sync_host(grid) has returned (read them only then). Pinned host
+ * memory is needed for the overlap. */
+lfp_status lfp_render_to_host_async(lfp_grid* grid, const lfp_view* views, int n_views,
+                                    float* rgb_host, uint8_t* cls_host, void* cuda_stream);
+/* Wait for every copy queued by lfp_render_to_host_async on this grid. */
+lfp_status lfp_sync_host(lfp_grid* grid);
+
 /* Adjoint of lfp_render with respect to radiance (the paper has no adjoint;
  * it follows from L_o(X, w1) = L_p(w2): for fixed distance and normal maps
  * the HIT texel and bilinear weights do not depend on radiance, so

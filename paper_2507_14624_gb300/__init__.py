@@ -235,6 +235,16 @@ class ProbeGrid:
         lfp.lfp_render_to_host(self.handle, arr, n, ctypes.c_void_p(rgb_host.data_ptr()),
                                ctypes.c_void_p(cls_host.data_ptr()), _stream_handle(stream))
 
+    def render_to_host_async(self, views, rgb_host, cls_host, stream=None):
+        """Queue a render whose rgb / cls land in the given pinned host tensors
+        (lfp_render_to_host_async); they are complete after sync_host()."""
+        arr, n, total = make_views(views)
+        lfp.lfp_render_to_host_async(self.handle, arr, n, ctypes.c_void_p(rgb_host.data_ptr()),
+                                     ctypes.c_void_p(cls_host.data_ptr()), _stream_handle(stream))
+
+    def sync_host(self):
+        lfp.lfp_sync_host(self.handle)
+
     def check_flags(self, stream=None) -> int:
         return lfp.lfp_check_flags(self.handle, _stream_handle(stream))
 

@@ -34,6 +34,15 @@ struct lfp_grid {
     float* host_rgb = nullptr;          // device buffers behind lfp_render_to_host
     uint8_t* host_cls = nullptr;
     long long host_pixels = 0;
+    // lfp_render_to_host_async: two device output buffers used in turn, a
+    // copy stream, and per buffer an event for "rendered" and "copied out"
+    float* async_rgb[2] = {nullptr, nullptr};
+    uint8_t* async_cls[2] = {nullptr, nullptr};
+    long long async_pixels = 0;
+    int async_slot = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t rendered[2] = {nullptr, nullptr};
+    cudaEvent_t copied[2] = {nullptr, nullptr};
     std::vector<unsigned char> uploaded;
     int tile_w = 16, tile_h = 8;        // default ray tile (nested engine)
     int stream_blocks = 0;              // persistent grid of the stream engine (0 = not sized yet)
@@ -266,6 +275,13 @@ void destroy(lfp_grid* g) {
     dev_free(g->keys);
     dev_free(g->host_rgb);
     dev_free(g->host_cls);
+    for (int k = 0; k < 2; ++k) {
+        dev_free(g->async_rgb[k]);
+        dev_free(g->async_cls[k]);
+        if (g->rendered[k]) cudaEventDestroy(g->rendered[k]);
+        if (g->copied[k]) cudaEventDestroy(g->copied[k]);
+    }
+    if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     delete g;
 }
 
@@ -621,6 +637,66 @@ lfp_status lfp_render_to_host(lfp_grid* g, const lfp_view* views, int n_views, f
     if (rgb_host) LFP_CUDA(cudaMemcpyAsync(rgb_host, g->host_rgb, total * 12, cudaMemcpyDeviceToHost, s));
     if (cls_host) LFP_CUDA(cudaMemcpyAsync(cls_host, g->host_cls, total, cudaMemcpyDeviceToHost, s));
     LFP_CUDA(cudaStreamSynchronize(s));
+    return LFP_OK;
+}
+
+lfp_status lfp_render_to_host_async(lfp_grid* g, const lfp_view* views, int n_views, float* rgb_host,
+                                    uint8_t* cls_host, void* stream) {
+    if (!g) return LFP_ERR_INVALID_ARG;
+    LFP_TRY(check_views(views, n_views));
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g->copy_stream) {
+        LFP_CUDA(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            LFP_CUDA(cudaEventCreateWithFlags(&g->rendered[k], cudaEventDisableTiming));
+            LFP_CUDA(cudaEventCreateWithFlags(&g->copied[k], cudaEventDisableTiming));
+        }
+    }
+    long long total = 0;
+    for (int i = 0; i < n_views; ++i)
+        total = std::max(total, views[i].out_offset + (long long)views[i].W * views[i].H);
+    if (total > g->async_pixels) {  // grow both buffers once nothing uses them
+        LFP_CUDA(cudaStreamSynchronize(g->copy_stream));
+        LFP_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < 2; ++k) {
+            dev_free(g->async_rgb[k]);
+            dev_free(g->async_cls[k]);
+            g->async_rgb[k] = nullptr;
+            g->async_cls[k] = nullptr;
+        }
+        g->async_pixels = 0;
+        for (int k = 0; k < 2; ++k) {
+            LFP_TRY(dev_alloc((void**)&g->async_rgb[k], total * 12));
+            LFP_TRY(dev_alloc((void**)&g->async_cls[k], total));
+        }
+        g->async_pixels = total;
+    }
+    const int k = g->async_slot;
+    g->async_slot ^= 1;
+    // the buffer's previous copy (two calls ago) must be out before it is reused
+    LFP_CUDA(cudaStreamWaitEvent(s, g->copied[k], 0));
+    OutDev out;
+    std::memset(&out, 0, sizeof(out));
+    out.rgb = g->async_rgb[k];
+    out.cls = g->async_cls[k];
+    LFP_TRY(render_impl(g, views, n_views, out, nullptr, s));
+    LFP_CUDA(cudaEventRecord(g->rendered[k], s));
+    LFP_CUDA(cudaStreamWaitEvent(g->copy_stream, g->rendered[k], 0));
+    if (rgb_host)
+        LFP_CUDA(cudaMemcpyAsync(rgb_host, g->async_rgb[k], total * 12, cudaMemcpyDeviceToHost, g->copy_stream));
+    if (cls_host) LFP_CUDA(cudaMemcpyAsync(cls_host, g->async_cls[k], total, cudaMemcpyDeviceToHost, g->copy_stream));
+    LFP_CUDA(cudaEventRecord(g->copied[k], g->copy_stream));
+    return LFP_OK;
+}
+
+lfp_status lfp_sync_host(lfp_grid* g) {
+    if (!g) return LFP_ERR_INVALID_ARG;
+    if (!g->copy_stream) return LFP_OK;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return LFP_ERR_CUDA;
+    LFP_CUDA(cudaStreamSynchronize(g->copy_stream));
     return LFP_OK;
 }
 

@@ -82,6 +82,8 @@ def _load():
         "lfp_render": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp], i),
         "lfp_render_ex": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
         "lfp_render_to_host": ([vp, P(lfp_view), i, vp, vp, vp], i),
+        "lfp_render_to_host_async": ([vp, P(lfp_view), i, vp, vp, vp], i),
+        "lfp_sync_host": ([vp], i),
         "lfp_render_static": ([vp, P(lfp_view), i, P(lfp_outputs), vp], i),
         "lfp_autotune": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
         "lfp_render_backward": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, vp], i),
@@ -154,6 +156,14 @@ def lfp_autotune(grid, views, n_views, outputs: lfp_outputs, stream) -> lfp_rend
 
 def lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream) -> None:
     _check(_lib.lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream), "lfp_render_to_host")
+
+
+def lfp_render_to_host_async(grid, views, n_views, rgb_host, cls_host, stream) -> None:
+    _check(_lib.lfp_render_to_host_async(grid, views, n_views, rgb_host, cls_host, stream), "lfp_render_to_host_async")
+
+
+def lfp_sync_host(grid) -> None:
+    _check(_lib.lfp_sync_host(grid), "lfp_sync_host")
 
 
 def lfp_render_backward(grid, views, n_views, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, stream) -> None:

@@ -84,6 +84,8 @@ def test_null_arguments_are_rejected(lib):
     assert L.raw_call("lfp_render_backward", None, None, 1, None, None, None, None, None, None) == L.LFP_ERR_INVALID_ARG
     assert L.raw_call("lfp_set_radiance", None, None, None) == L.LFP_ERR_INVALID_ARG
     assert L.raw_call("lfp_check_flags", None, None) == L.LFP_ERR_INVALID_ARG
+    assert L.raw_call("lfp_render_to_host_async", None, None, 1, None, None, None) == L.LFP_ERR_INVALID_ARG
+    assert L.raw_call("lfp_sync_host", None) == L.LFP_ERR_INVALID_ARG
     assert L.raw_call("lfp_build_probes_from_points", None, 0, 1, None, 0.0, None) == L.LFP_ERR_INVALID_ARG
     assert L.raw_call("lfp_read_probes", None, 0, 1, None, None, None, None) == L.LFP_ERR_INVALID_ARG
     assert L.raw_call("lfp_pick_levels", None, 1, None, 1, None) == L.LFP_ERR_INVALID_ARG

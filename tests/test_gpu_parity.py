@@ -189,6 +189,26 @@ def test_render_to_host_matches_device_render(tiny):
     assert torch.equal(rgb, a["rgb"].cpu()) and torch.equal(cls, a["cls"].cpu())
 
 
+def test_render_to_host_async_frame_loop(tiny):
+    """Four frames (different views and sizes) through the double-buffered
+    host path: after lfp_sync_host every frame's host buffers equal the
+    device render of its views."""
+    sc, views, d, n, r = tiny
+    g = make_grid(sc, d, n, r)
+    frames = [[synth.random_view(sc, 900 + k, 64 + 16 * k, 48, 60.0)] for k in range(4)]
+    hosts = []
+    for vs in frames:
+        P = vs[0].n_pixels
+        rgb = torch.empty((P, 3), dtype=torch.float32).pin_memory()
+        cls = torch.empty(P, dtype=torch.uint8).pin_memory()
+        g.render_to_host_async(vs, rgb, cls)
+        hosts.append((rgb, cls))
+    g.sync_host()
+    for vs, (rgb, cls) in zip(frames, hosts):
+        ref = g.render(vs)
+        assert torch.equal(rgb, ref["rgb"].cpu()) and torch.equal(cls, ref["cls"].cpu())
+
+
 def test_step_limit_sets_class_and_flag(tiny):
     sc, views, d, n, r = tiny
     g = make_grid(sc, d, n, r, max_steps=3)
