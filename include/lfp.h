@@ -61,7 +61,7 @@ enum {
     LFP_CLASS_STEPLIMIT = 3  /* max_steps texel visits reached */
 };
 
-/* Grid of probes (Sec. 3 "probes are placed at the vertices of a uniform 3D grid").
+/* Grid of probes (Sec. 3: probes sit at the vertices of a uniform 3D grid).
  *   nx, ny, nz >= 2          probes per axis (cells: (nx-1)(ny-1)(nz-1));
  *                            >= 1 with traversal LFP_TRAVERSAL_NEAREST
  *   origin, spacing > 0      probe (0,0,0) position and grid pitch
@@ -73,7 +73,7 @@ enum {
  *                            nearest radial distance is <= d (1 + 4 th / N);
  *                            th < 0 selects the two-way rule of Appendix A
  *                            highResolutionTracing (every crossing -> normal test)
- *   eye_eps                  |X - O| < eye_eps is "eye aligned with a probe"
+ *   eye_eps                  |X - O| < eye_eps counts as the eye aligned with a probe
  *                            (Sec. 4.2, O(1) lookup); 0 -> 1e-6 * spacing
  *   max_steps                cap on texel visits per ray, 0 = none
  *   eye_lookup               LFP_EYE_BILINEAR (default): the eye-aligned
@@ -334,7 +334,7 @@ lfp_status lfp_build_probes_from_points(lfp_grid* grid, int first_probe, int cou
 lfp_status lfp_read_probes(lfp_grid* grid, int first_probe, int count, float* dist, float* normal, float* radiance,
                            void* cuda_stream);
 
-/* Multi-scale hierarchy (the "multi-scale, implicit representations" of the
+/* Multi-scale hierarchy (the multi-scale representation named in the
  * abstract; the hierarchical scene representation of the teaser figure):
  * several grids of one scene at different spacings, typically nested (coarse
  * grids over the whole scene, fine grids where the eye goes).

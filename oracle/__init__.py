@@ -308,8 +308,8 @@ def probe_box(grid):
 
 def pick_level(levels, X):
     """Level that traces a ray starting at X in a multi-scale hierarchy of
-    probe grids (the "multi-scale, implicit representations" of the abstract,
-    the hierarchical scene representation of the teaser figure): the finest
+    probe grids (the multi-scale representation named in the abstract, the
+    hierarchical scene representation of the teaser figure): the finest
     level (smallest spacing, ties to the lower index) whose probe box contains
     X; if none does, the coarsest (largest spacing, ties to the lower index)."""
     X = np.asarray(X, np.float64)

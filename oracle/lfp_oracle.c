@@ -25,7 +25,7 @@
  * Readings where the paper is silent (each also listed in the design notes):
  *   R1 octahedral pole +z; texel (i, j) covers u in [i/N, (i+1)/N) of
  *      u = (p + 1) / 2; storage row-major, j the row.
- *   R2 "low resolution derived by convolution" -> per-block min and max of
+ *   R2 low-resolution map (a convolution in the paper) -> per-block min and max of
  *      the distance map (block k x k, k = N / M); conservative, so the
  *      hierarchical march returns exactly what the flat march returns.
  *   R3 texel test over the ray's t-interval [ta, tb] inside the texel:
@@ -34,9 +34,9 @@
  *      r_hi < d -> the ray stays in front (continue); else r_lo <= thr(d) ->
  *      crossing, normal . w < 0 -> HIT else UNKNOWN; else (the ray passes
  *      behind the stored surface) -> UNKNOWN. The listing's highResolution-
- *      Tracing sends every crossing straight to the normal test; the text's
- *      "the ray can shoot from below the surface ... UNKNOWN" is read as the
- *      passes-behind branch. th < 0 selects the listing's two-way rule.
+ *      Tracing sends every crossing straight to the normal test; the text
+ *      explains UNKNOWN by a ray that may start underneath the surface, read
+ *      as the passes-behind branch. th < 0 selects the listing's two-way rule.
  *      Coarse texel: candidate iff r_hi >= dmin.
  *   R4 hit point (the listing returns the texel only): the first t >= ta at
  *      which the ray reaches the stored distance, r(t) = d, clamped to
@@ -452,7 +452,7 @@ static double hit_time(const oseg* sg, double ta, double tb, double d) {
     return clampd((-B - sqrt(disc)) / A, ta, tb); /* approaching: the smaller root */
 }
 
-/* Octant split (Sec. 4.2: "at most 4 ray segments"): cut [t0, t1] where the
+/* Octant split (Sec. 4.2: no more than four segments): cut [t0, t1] where the
  * ray crosses the probe's three axis planes. Returns the number of segments. */
 int orc_split_segments(const double X[3], const double w[3], const double O[3],
                        double t0, double t1, double* bounds /* [5] */) {

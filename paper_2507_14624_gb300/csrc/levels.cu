@@ -1,6 +1,6 @@
-// Multi-scale hierarchy of probe grids (the "multi-scale, implicit
-// representations" of the abstract; the hierarchical scene representation of
-// the teaser figure). Every ray of a view starts at the camera, so the level
+// Multi-scale hierarchy of probe grids (the multi-scale representation named
+// in the abstract; the hierarchical scene representation of the teaser
+// figure). Every ray of a view starts at the camera, so the level
 // that traces a ray is a per-view choice: the views are grouped by level on
 // the host and each group is one render (or adjoint) call on its grid, into
 // the caller's shared flat outputs at each view's own out_offset.
