@@ -223,6 +223,10 @@ def run_lfp(args):
     grid = lfpk.ProbeGrid(sc.grid, radiance_fmt=fmt, normal_fmt=fmt, traversal=trav)
     grid.upload(d, n, r)
     sched = lfpk.LFP_SCHED_PERSISTENT if len(views) > 1 else 0
+    tuned = None
+    if len(views) > 1:  # the batched form: launch configuration picked by the autotuner
+        tuned = grid.autotune(views)
+        sched = 0
     arr, nv, total = lfpk.make_views(views)
     dev = torch.device("cuda", local)
     rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
@@ -326,6 +330,7 @@ def run_lfp(args):
                 "dtype": "f16+f32" if f16 else "f32", "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
                 "config": workload_info(args.workload, views, sc.grid), "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cuda_graph": graph is not None,
+                "autotuned": tuned,
                 "roofline": roofline, "clocks": clk,
                 "cpu_baseline": cpu, **extra}
         print(json.dumps(line), flush=True)
@@ -503,6 +508,11 @@ def run_multiscale(args):
     arr, nv, total = lfpk.make_views(views)
     lev = h.level_of(views)
     launches_per_step = len(set(lev))
+    tuned = {}
+    for k, g in enumerate(h.grids):  # each level's launch configuration from the autotuner
+        mine = [v for v, l in zip(views, lev) if l == k]
+        if mine:
+            tuned[str(k)] = g.autotune(mine)
     graph, out = h.render_graph(views, aux=False)
 
     cnt = torch.zeros(lfp.N_COUNTERS, dtype=torch.int64, device=dev)
@@ -621,7 +631,8 @@ def run_multiscale(args):
                            "views_per_level": per_level, "l2": "flushed before every timed step (256 MiB write)"},
                 "e2e": {"value": round(e2e_value, 3), "unit": "Mrays/s", "h2d_bytes_per_step": int(nv * 72),
                         "d2h_bytes_per_step": int(total * 13)},
-                "gpu_launches": launches_per_step * args.steps, "cuda_graph": True, "roofline": roofline,
+                "gpu_launches": launches_per_step * args.steps, "cuda_graph": True, "autotuned": tuned,
+                "roofline": roofline,
                 "clocks": clk, "cpu_baseline": cpu, "fwd_adj_ms_per_view": round(fwd_adj, 4)}
         print(json.dumps(line), flush=True)
     for g in h.grids:

@@ -164,7 +164,13 @@ typedef struct {
                        loop nest of Appendix A, one ray per thread (tile_w,
                        tile_h, schedule and LFP_MARCH_FLAT apply to it only).
                        Both give identical results. */
+    int occupancy;  /* streaming engine: LFP_OCC_AUTO (the grid's default,
+                       set by lfp_autotune), LFP_OCC_8 (8 blocks of 128
+                       threads per SM, up to 64 registers per thread) or
+                       LFP_OCC_9 (9 blocks, up to 56 registers); identical
+                       results, different speed per workload */
 } lfp_render_opts;
+enum { LFP_OCC_AUTO = 0, LFP_OCC_8 = 1, LFP_OCC_9 = 2 };
 
 /* Create a grid; allocates the device planes for all nx*ny*nz probes on the
  * current device. *out receives the handle (owned by the caller, release with

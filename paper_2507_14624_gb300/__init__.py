@@ -147,7 +147,7 @@ class ProbeGrid:
         lfp.lfp_set_radiance(self.handle, ctypes.c_void_p(r.data_ptr()), _stream_handle(stream))
 
     def render(self, views, aux=True, hit_texel=False, counters=False, march=LFP_MARCH_HIER, tile=None,
-               schedule=0, engine=0, stream=None):
+               schedule=0, engine=0, occupancy=0, stream=None):
         """Render views; returns a dict of CUDA tensors: rgb [P,3] f32,
         cls [P] u8, and optionally probe [P] i32, uv [P,2] f32, texel [P] i32,
         counters [8] i64 (see lfp.COUNTER_NAMES)."""
@@ -175,6 +175,7 @@ class ProbeGrid:
             opts.tile_w, opts.tile_h = tile
         opts.schedule = schedule
         opts.engine = engine
+        opts.occupancy = occupancy
         lfp.lfp_render_ex(self.handle, arr, n, o, opts, _stream_handle(stream))
         return out
 
@@ -189,7 +190,7 @@ class ProbeGrid:
         o = lfp.lfp_outputs()
         o.rgb, o.cls = rgb.data_ptr(), cls.data_ptr()
         b = lfp.lfp_autotune(self.handle, arr, n, o, _stream_handle(stream))
-        return {"engine": b.engine, "tile": (b.tile_w, b.tile_h), "schedule": b.schedule}
+        return {"engine": b.engine, "tile": (b.tile_w, b.tile_h), "schedule": b.schedule, "occupancy": b.occupancy}
 
     def render_graph(self, views, aux=False, stream=None):
         """Capture one render of these views in a CUDA graph (outputs are

@@ -45,7 +45,8 @@ struct lfp_grid {
     cudaEvent_t copied[2] = {nullptr, nullptr};
     std::vector<unsigned char> uploaded;
     int tile_w = 16, tile_h = 8;        // default ray tile (nested engine)
-    int stream_blocks = 0;              // persistent grid of the stream engine (0 = not sized yet)
+    int stream_blocks[2] = {0, 0};      // persistent grid of the stream engine per register budget
+    int stream_occ = 0;                 // default register budget (0: 8 blocks/SM, 1: 9; lfp_autotune)
     int engine = LFP_ENGINE_STREAM;     // default engine (set by lfp_autotune)
     int schedule = LFP_SCHED_TILES;
 };
@@ -189,10 +190,12 @@ bool valid_tile(int w, int h) {
 
 lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const OutDev& out,
                        const lfp_render_opts* opts, cudaStream_t s) {
-    int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0, engine = g->engine;
+    int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0, engine = g->engine, occ = g->stream_occ;
     if (opts) {
         if (opts->engine < LFP_ENGINE_AUTO || opts->engine > LFP_ENGINE_NESTED) return LFP_ERR_INVALID_ARG;
         if (opts->engine != LFP_ENGINE_AUTO) engine = opts->engine;
+        if (opts->occupancy < LFP_OCC_AUTO || opts->occupancy > LFP_OCC_9) return LFP_ERR_INVALID_ARG;
+        if (opts->occupancy != LFP_OCC_AUTO) occ = opts->occupancy == LFP_OCC_9 ? 1 : 0;
         if (opts->tile_w || opts->tile_h) {
             if (!valid_tile(opts->tile_w, opts->tile_h)) return LFP_ERR_INVALID_ARG;
             tw = opts->tile_w;
@@ -210,9 +213,9 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
     // the streaming engine runs the grid traversal with the hierarchical
     // march; the flat march and the nearest-probe traversal run on the loop nest
     if (engine == LFP_ENGINE_STREAM && !flat && g->desc.traversal == LFP_TRAVERSAL_GRID) {
-        if (g->stream_blocks == 0)
-            g->stream_blocks = std::max(1, render_stream_blocks_per_sm(g->desc.radiance_fmt, g->desc.normal_fmt)) *
-                               g->sm_count;
+        if (g->stream_blocks[occ] == 0)
+            g->stream_blocks[occ] =
+                std::max(1, render_stream_blocks_per_sm(g->desc.radiance_fmt, g->desc.normal_fmt, occ)) * g->sm_count;
         for (int first = 0; first < n_views; first += kMaxViewsPerLaunch) {
             int n = std::min(kMaxViewsPerLaunch, n_views - first);
             vb.n = n;
@@ -226,10 +229,10 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
                 if (tiles > (1LL << 31) - 1) return LFP_ERR_INVALID_ARG;
             }
             vb.total_tiles = (int)tiles;
-            int blocks = (int)std::min<long long>(g->stream_blocks, (tiles + 3) / 4);
+            int blocks = (int)std::min<long long>(g->stream_blocks[occ], (tiles + 3) / 4);
             LFP_CUDA(cudaMemsetAsync(g->tile_counter, 0, sizeof(unsigned), s));
             LFP_CUDA(launch_render_stream(gd, g->desc.radiance_fmt, g->desc.normal_fmt, vb, out, g->tile_counter,
-                                          blocks, s));
+                                          blocks, occ, s));
         }
         return LFP_OK;
     }
@@ -558,8 +561,12 @@ lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const l
     std::vector<lfp_render_opts> cand;
     lfp_render_opts c;
     std::memset(&c, 0, sizeof(c));
-    c.engine = LFP_ENGINE_STREAM;
-    if (g->desc.traversal == LFP_TRAVERSAL_GRID) cand.push_back(c);
+    if (g->desc.traversal == LFP_TRAVERSAL_GRID)
+        for (int oc : {LFP_OCC_8, LFP_OCC_9}) {
+            c.engine = LFP_ENGINE_STREAM;
+            c.occupancy = oc;
+            cand.push_back(c);
+        }
     const int shapes[5][2] = {{8, 4}, {8, 8}, {16, 8}, {16, 16}, {32, 8}};
     for (auto& sh : shapes)
         for (int sched : {LFP_SCHED_TILES, LFP_SCHED_PERSISTENT}) {
@@ -599,6 +606,7 @@ lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const l
     cudaEventDestroy(e1);
     if (st != LFP_OK) return st;
     g->engine = pick.engine;
+    if (pick.engine == LFP_ENGINE_STREAM) g->stream_occ = pick.occupancy == LFP_OCC_9 ? 1 : 0;
     if (pick.engine == LFP_ENGINE_NESTED) {
         g->tile_w = pick.tile_w;
         g->tile_h = pick.tile_h;

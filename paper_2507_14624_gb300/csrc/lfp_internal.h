@@ -20,10 +20,11 @@ cudaError_t launch_render(const GridDev& g, int rad_fmt, int nrm_fmt, const View
                           const RenderLaunch& L, cudaStream_t s);
 int render_max_active_blocks(int rad_fmt, int nrm_fmt, int threads);
 // streaming engine (render_stream.cu): vb built with 8x4 ray tiles; queue
-// zeroed by the caller; blocks = SMs x render_stream_blocks_per_sm
+// zeroed by the caller; blocks = SMs x render_stream_blocks_per_sm; occ 0:
+// 8 blocks per SM (64 registers), 1: 9 blocks per SM (56 registers)
 cudaError_t launch_render_stream(const GridDev& g, int rad_fmt, int nrm_fmt, const ViewBatch& vb, const OutDev& out,
-                                 unsigned* queue, int blocks, cudaStream_t s);
-int render_stream_blocks_per_sm(int rad_fmt, int nrm_fmt);
+                                 unsigned* queue, int blocks, int occ, cudaStream_t s);
+int render_stream_blocks_per_sm(int rad_fmt, int nrm_fmt, int occ);
 
 // upload-time conversions: xyz normals -> octahedral RG, RGB -> RGBA texels
 cudaError_t launch_encode_normals(const float* xyz, void* nrm, int nrm_fmt, long long n, cudaStream_t s);

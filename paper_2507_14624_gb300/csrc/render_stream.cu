@@ -29,9 +29,8 @@ using namespace trace;
 #ifndef LFP_STREAM_BATCH_PCT
 #define LFP_STREAM_BATCH_PCT 75
 #endif
-#ifndef LFP_STREAM_MIN_BLOCKS
-#define LFP_STREAM_MIN_BLOCKS 8
-#endif
+// resident blocks per SM of the two register budgets (64 and 56 registers)
+constexpr int kMinBlocks[2] = {8, 9};
 constexpr int kStreamThreads = 128;
 constexpr int kWalkSteps = LFP_STREAM_WALK_STEPS;  // most texel visits per lane between control rounds
 constexpr int kBatchPct = LFP_STREAM_BATCH_PCT;     // transitions run once this % of busy lanes wait
@@ -474,9 +473,9 @@ __device__ __forceinline__ void write_ray(const GridDev& g, const OutDev& out, c
 // its 32 lanes busy, one texel visit per lane per iteration. COUNT selects
 // the instrumented variant (fetch counters and the max_steps cap); the plain
 // variant carries neither, which keeps the per-visit path short.
-template <int RADF, int NRMF, bool COUNT>
-__global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_stream_kernel(GridDev g, ViewBatch vb, OutDev out,
-                                                                          unsigned* queue) {
+template <int RADF, int NRMF, bool COUNT, int OCC>
+__global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream_kernel(GridDev g, ViewBatch vb,
+                                                                                     OutDev out, unsigned* queue) {
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
     Lane L;
@@ -606,35 +605,42 @@ __global__ void __launch_bounds__(kStreamThreads, LFP_STREAM_MIN_BLOCKS) render_
 
 template <int RADF, int NRMF>
 cudaError_t launch_stream_fmt(const GridDev& g, const ViewBatch& vb, const OutDev& out, unsigned* queue, int blocks,
-                              cudaStream_t s) {
+                              int occ, cudaStream_t s) {
+    // the instrumented variant (counters, step cap) always uses the 64-register budget
     if (out.counters || g.max_steps > 0)
-        render_stream_kernel<RADF, NRMF, true><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+        render_stream_kernel<RADF, NRMF, true, 0><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+    else if (occ == 1)
+        render_stream_kernel<RADF, NRMF, false, 1><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
     else
-        render_stream_kernel<RADF, NRMF, false><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+        render_stream_kernel<RADF, NRMF, false, 0><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
     return cudaGetLastError();
+}
+
+template <int RADF, int NRMF>
+int blocks_fmt(int occ) {
+    int n = 0;
+    if (occ == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<RADF, NRMF, false, 1>, kStreamThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<RADF, NRMF, false, 0>, kStreamThreads, 0);
+    return n;
 }
 
 }  // namespace
 
 cudaError_t launch_render_stream(const GridDev& g, int rad_fmt, int nrm_fmt, const ViewBatch& vb, const OutDev& out,
-                                 unsigned* queue, int blocks, cudaStream_t s) {
-    if (rad_fmt == kF32 && nrm_fmt == kF32) return launch_stream_fmt<kF32, kF32>(g, vb, out, queue, blocks, s);
-    if (rad_fmt == kF16 && nrm_fmt == kF16) return launch_stream_fmt<kF16, kF16>(g, vb, out, queue, blocks, s);
-    if (rad_fmt == kF16 && nrm_fmt == kF32) return launch_stream_fmt<kF16, kF32>(g, vb, out, queue, blocks, s);
-    return launch_stream_fmt<kF32, kF16>(g, vb, out, queue, blocks, s);
+                                 unsigned* queue, int blocks, int occ, cudaStream_t s) {
+    if (rad_fmt == kF32 && nrm_fmt == kF32) return launch_stream_fmt<kF32, kF32>(g, vb, out, queue, blocks, occ, s);
+    if (rad_fmt == kF16 && nrm_fmt == kF16) return launch_stream_fmt<kF16, kF16>(g, vb, out, queue, blocks, occ, s);
+    if (rad_fmt == kF16 && nrm_fmt == kF32) return launch_stream_fmt<kF16, kF32>(g, vb, out, queue, blocks, occ, s);
+    return launch_stream_fmt<kF32, kF16>(g, vb, out, queue, blocks, occ, s);
 }
 
-int render_stream_blocks_per_sm(int rad_fmt, int nrm_fmt) {
-    int n = 0;
-    if (rad_fmt == kF32 && nrm_fmt == kF32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<kF32, kF32, false>, kStreamThreads, 0);
-    else if (rad_fmt == kF16 && nrm_fmt == kF16)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<kF16, kF16, false>, kStreamThreads, 0);
-    else if (rad_fmt == kF16)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<kF16, kF32, false>, kStreamThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<kF32, kF16, false>, kStreamThreads, 0);
-    return n;
+int render_stream_blocks_per_sm(int rad_fmt, int nrm_fmt, int occ) {
+    if (rad_fmt == kF32 && nrm_fmt == kF32) return blocks_fmt<kF32, kF32>(occ);
+    if (rad_fmt == kF16 && nrm_fmt == kF16) return blocks_fmt<kF16, kF16>(occ);
+    if (rad_fmt == kF16) return blocks_fmt<kF16, kF32>(occ);
+    return blocks_fmt<kF32, kF16>(occ);
 }
 
 }  // namespace lfp

@@ -23,6 +23,7 @@ LFP_MARCH_HIER, LFP_MARCH_FLAT = 0, 1
 LFP_SCHED_AUTO, LFP_SCHED_TILES, LFP_SCHED_PERSISTENT = 0, 1, 2
 LFP_ENGINE_AUTO, LFP_ENGINE_STREAM, LFP_ENGINE_NESTED = 0, 1, 2
 LFP_REDUCE_AUTO, LFP_REDUCE_ATOMIC, LFP_REDUCE_WARP, LFP_REDUCE_SORT = 0, 1, 2, 3
+LFP_OCC_AUTO, LFP_OCC_8, LFP_OCC_9 = 0, 1, 2
 LFP_EYE_BILINEAR, LFP_EYE_NEAREST = 0, 1
 LFP_TRAVERSAL_GRID, LFP_TRAVERSAL_NEAREST = 0, 1
 LFP_NEAREST_MAX_PROBES = 8
@@ -57,7 +58,7 @@ class lfp_outputs(ctypes.Structure):
 
 class lfp_render_opts(ctypes.Structure):
     _fields_ = [("march", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("engine", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("engine", ctypes.c_int), ("occupancy", ctypes.c_int)]
 
 
 class lfp_point_cloud(ctypes.Structure):

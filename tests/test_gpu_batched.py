@@ -45,6 +45,8 @@ def test_autotune_keeps_results_and_sets_a_default():
     assert best["engine"] in (lfpk.LFP_ENGINE_STREAM, lfpk.LFP_ENGINE_NESTED)
     if best["engine"] == lfpk.LFP_ENGINE_NESTED:
         assert best["tile"] in ((8, 4), (8, 8), (16, 8), (16, 16), (32, 8))
+    else:
+        assert best["occupancy"] in (lfpk.lfp.LFP_OCC_8, lfpk.lfp.LFP_OCC_9)
     after = g.render(vs, hit_texel=True)  # default options now follow the tuned config
     for k in ("cls", "probe", "texel"):
         assert torch.equal(before[k], after[k]), k
