@@ -299,7 +299,9 @@ lfp_status lfp_render_static(lfp_grid* grid, const lfp_view* views, int n_views,
  *           Sec. 5.1 gives its normal map
  *   n       1 .. 2^32 - 1 points
  *   is_device 1: device pointers, read in place; 0: host pointers, copied
- *           into temporary device buffers (the call then synchronises) */
+ *           on the stream into a grid-owned device buffer (kept for later
+ *           calls); pinned host memory copies asynchronously and must stay
+ *           valid until the stream has passed the call */
 typedef struct {
     const float* xyz;
     const float* rgb;

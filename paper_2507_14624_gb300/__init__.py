@@ -107,7 +107,8 @@ class ProbeGrid:
     def build_from_points(self, xyz, rgb, normal=None, first_probe=0, count=None, empty_dist=0.0, stream=None):
         """Fill probes [first_probe, first_probe + count) from a point cloud
         (lfp_build_probes_from_points): xyz, rgb, optional normal [n][3]
-        float32, numpy (host) or CUDA tensors (device)."""
+        float32: CUDA tensors (read in place), or numpy arrays / CPU tensors
+        (copied; pinned CPU tensors copy asynchronously)."""
         import numpy as np
         import torch
         count = self.n_probes - first_probe if count is None else count
@@ -116,10 +117,10 @@ class ProbeGrid:
         if isinstance(xyz, torch.Tensor):
             keep = [t.contiguous() for t in arrays]
             for t in keep:
-                if t.dtype != torch.float32 or not t.is_cuda:
-                    raise ValueError("device point clouds must be CUDA float32 tensors")
+                if t.dtype != torch.float32 or t.is_cuda != keep[0].is_cuda:
+                    raise ValueError("point clouds must be float32 tensors on one device")
             ptr = [t.data_ptr() for t in keep]
-            pc.is_device = 1
+            pc.is_device = 1 if keep[0].is_cuda else 0
         else:
             keep = [np.ascontiguousarray(a, dtype=np.float32) for a in arrays]
             ptr = [a.ctypes.data for a in keep]
@@ -128,6 +129,8 @@ class ProbeGrid:
         pc.normal = ptr[2] if normal is not None else None
         pc.n = keep[0].shape[0]
         lfp.lfp_build_probes_from_points(self.handle, first_probe, count, pc, empty_dist, _stream_handle(stream))
+        if not pc.is_device:  # host planes must outlive the asynchronous copies
+            torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
 
     def read_probes(self, first_probe=0, count=None, stream=None):
         """(dist [c][N][N], normal [c][N][N][3], radiance [c][N][N][3]) float32 CUDA tensors."""

@@ -31,6 +31,8 @@ struct lfp_grid {
     size_t staging_bytes = 0;
     unsigned long long* keys = nullptr; // point-cloud builder: nearest-point table
     size_t keys_bytes = 0;
+    float* cloud = nullptr;             // point-cloud builder: device copy of a host cloud
+    size_t cloud_bytes = 0;
     float* host_rgb = nullptr;          // device buffers behind lfp_render_to_host
     uint8_t* host_cls = nullptr;
     long long host_pixels = 0;
@@ -276,6 +278,7 @@ void destroy(lfp_grid* g) {
     dev_free(g->tile_counter);
     dev_free(g->staging);
     dev_free(g->keys);
+    dev_free(g->cloud);
     dev_free(g->host_rgb);
     dev_free(g->host_cls);
     for (int k = 0; k < 2; ++k) {
@@ -442,22 +445,19 @@ lfp_status lfp_build_probes_from_points(lfp_grid* g, int first_probe, int count,
     const int N = g->desc.N;
     const size_t NN = (size_t)N * N;
     const long long n = pc->n;
-    // host clouds are copied into temporary device buffers, freed at the end
+    // host clouds are copied into a grid-owned device buffer (kept for the
+    // next call); the copies are ordered on the stream like the kernels
     const float *xyz = pc->xyz, *rgb = pc->rgb, *nrm = pc->normal;
-    float* tmp = nullptr;
     if (!pc->is_device) {
         size_t planes = nrm ? 3 : 2;
-        LFP_TRY(dev_alloc((void**)&tmp, planes * n * 12));
-        cudaError_t e = cudaMemcpyAsync(tmp, pc->xyz, n * 12, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp + 3 * n, pc->rgb, n * 12, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && nrm) e = cudaMemcpyAsync(tmp + 6 * n, pc->normal, n * 12, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) {
-            dev_free(tmp);
-            return LFP_ERR_CUDA;
-        }
-        xyz = tmp;
-        rgb = tmp + 3 * n;
-        nrm = nrm ? tmp + 6 * n : nullptr;
+        LFP_TRY(ensure(&g->cloud, &g->cloud_bytes, planes * n * 12, s));
+        float* c = g->cloud;
+        LFP_CUDA(cudaMemcpyAsync(c, pc->xyz, n * 12, cudaMemcpyHostToDevice, s));
+        LFP_CUDA(cudaMemcpyAsync(c + 3 * n, pc->rgb, n * 12, cudaMemcpyHostToDevice, s));
+        if (nrm) LFP_CUDA(cudaMemcpyAsync(c + 6 * n, pc->normal, n * 12, cudaMemcpyHostToDevice, s));
+        xyz = c;
+        rgb = c + 3 * n;
+        nrm = nrm ? c + 6 * n : nullptr;
     }
     // chunk of probes whose key table fits a 64 MiB slice of L2
     const int chunk = (int)std::max<size_t>(
@@ -487,10 +487,6 @@ lfp_status lfp_build_probes_from_points(lfp_grid* g, int first_probe, int count,
         launch_build_mip(g->dist + (size_t)first_probe * NN, g->mip + (size_t)first_probe * g->desc.M * g->desc.M,
                          count, N, g->desc.M, s) != cudaSuccess)
         st = LFP_ERR_CUDA;
-    if (tmp) {
-        if (cudaStreamSynchronize(s) != cudaSuccess) st = LFP_ERR_CUDA;
-        dev_free(tmp);
-    }
     if (st == LFP_OK)
         for (int p = first_probe; p < first_probe + count; ++p) g->uploaded[p] = 1;
     return st;

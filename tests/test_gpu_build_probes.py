@@ -55,6 +55,12 @@ def test_device_cloud_and_split_calls_equal_one_host_call():
     b.build_from_points(xyz, rgb, first_probe=3, count=5)
     for x, y in zip(a.read_probes(), b.read_probes()):
         assert torch.equal(x, y)
+    c = lfpk.ProbeGrid(sc.grid)  # pinned host tensors, built twice (buffer reused)
+    xyz_h, rgb_h = (torch.from_numpy(pc[k]).pin_memory() for k in ("xyz", "rgb"))
+    c.build_from_points(xyz_h, rgb_h)
+    c.build_from_points(xyz_h, rgb_h)
+    for x, y in zip(a.read_probes(), c.read_probes()):
+        assert torch.equal(x, y)
 
 
 def test_render_from_built_probes_matches_oracle():
