@@ -16,7 +16,7 @@ views, and SM clocks sampled during the timed region.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lfp|reference]
                   [--workload room|batched|fit|few|multiscale|build|sweep]
 (few: four probes, the nearest-probe traversal Sec. 4.3 gives for fewer than
-8 probes, on the loop-nest kernel.)
+8 probes.)
 Under torchrun every rank renders its own copy of the workload (weak scaling,
 no collective on the data path); rank 0 prints the JSON line.
 """
@@ -125,9 +125,8 @@ class ClockSampler:
 
 
 def kernel_of(workload):
-    """The kernel that renders the workload: the nearest-probe traversal runs
-    on the loop-nest engine, the grid traversal on the streaming engine."""
-    return "render_kernel" if workload == "few" else "render_stream_kernel"
+    """The kernel that renders the workload (the streaming engine for all)."""
+    return "render_stream_kernel"
 
 
 def render_source_sha(workload="room"):

@@ -85,8 +85,7 @@ enum {
  *                            LFP_TRAVERSAL_NEAREST: the mode Sec. 4.3 gives
  *                            for fewer than 8 probes: all probes (at most 8)
  *                            nearest to the eye first, each traced over the
- *                            whole ray; MISS or UNKNOWN goes to the next probe.
- *                            Runs on the loop-nest engine. */
+ *                            whole ray; MISS or UNKNOWN goes to the next probe. */
 enum { LFP_EYE_BILINEAR = 0, LFP_EYE_NEAREST = 1 };
 enum { LFP_TRAVERSAL_GRID = 0, LFP_TRAVERSAL_NEAREST = 1 };
 #define LFP_NEAREST_MAX_PROBES 8

@@ -212,9 +212,9 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
         if (!u) return LFP_ERR_STATE;
     GridDev gd = grid_dev(g);
     static thread_local ViewBatch vb;  // ~10 KB: keep it off the host stack
-    // the streaming engine runs the grid traversal with the hierarchical
-    // march; the flat march and the nearest-probe traversal run on the loop nest
-    if (engine == LFP_ENGINE_STREAM && !flat && g->desc.traversal == LFP_TRAVERSAL_GRID) {
+    // the streaming engine runs the hierarchical march (both traversals); the
+    // flat march runs on the loop nest
+    if (engine == LFP_ENGINE_STREAM && !flat) {
         if (g->stream_blocks[occ] == 0)
             g->stream_blocks[occ] =
                 std::max(1, render_stream_blocks_per_sm(g->desc.radiance_fmt, g->desc.normal_fmt, occ)) * g->sm_count;
@@ -557,8 +557,8 @@ lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const l
     std::vector<lfp_render_opts> cand;
     lfp_render_opts c;
     std::memset(&c, 0, sizeof(c));
-    if (g->desc.traversal == LFP_TRAVERSAL_GRID)
-        for (int oc : {LFP_OCC_8, LFP_OCC_9}) {
+    for (int oc : {LFP_OCC_8, LFP_OCC_9})
+        if (oc == LFP_OCC_8 || g->desc.traversal == LFP_TRAVERSAL_GRID) {
             c.engine = LFP_ENGINE_STREAM;
             c.occupancy = oc;
             cand.push_back(c);

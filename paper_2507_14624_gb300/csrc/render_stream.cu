@@ -160,13 +160,20 @@ __device__ __forceinline__ void cell_start(const GridDev& g) {
     CI(kQ) = 0;
 }
 
+// Position of the current probe: a corner of the cell's cage, or (nearest-
+// probe traversal) the probe whose index is stored in kKq.
+template <bool NEAREST>
+__device__ __forceinline__ float3 current_probe_pos(const GridDev& g) {
+    return NEAREST ? probe_pos(g, CI(kKq)) : corner_pos(g, CI(kC0), CI(kC1), CI(kC2), CI(kKq));
+}
+
 // Probe of rank q: its index and the cut points of the octant split.
+template <bool NEAREST>
 __device__ __forceinline__ void probe_start(const GridDev& g, Lane& L) {
     const int kq = ((unsigned)CI(kOrder) >> (3 * CI(kQ))) & 7;
-    const int c0 = CI(kC0), c1 = CI(kC1), c2 = CI(kC2);
     CI(kKq) = kq;
-    L.probe = corner_index(g, c0, c1, c2, kq);
-    float3 O = corner_pos(g, c0, c1, c2, kq);
+    L.probe = NEAREST ? kq : corner_index(g, CI(kC0), CI(kC1), CI(kC2), kq);
+    float3 O = current_probe_pos<NEAREST>(g);
     const float3 X = ray_X(), w = ray_w();
     const float t0 = CF(kTin), t1 = CF(kTout);
     float cx = w.x != 0.0f ? (O.x - X.x) * frcp(w.x) : kInf;
@@ -195,6 +202,7 @@ __device__ __forceinline__ void coarse_box(const GridDev& g, Lane& L) {
 
 // Segment segi: the octant line (same arithmetic as seg_setup) and the
 // start of the low-resolution walk.
+template <bool NEAREST>
 __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     const int segi = CI(kSegI);
     float b = segi == 0 ? CF(kCut0) : (segi == 1 ? CF(kCut1) : (segi == 2 ? CF(kCut2) : kInf));
@@ -202,7 +210,7 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     CI(kSegFinal) = final_seg;
     if (final_seg) b = CF(kTout);
     CF(kSegB) = b;
-    float3 O = corner_pos(g, CI(kC0), CI(kC1), CI(kC2), CI(kKq));
+    float3 O = current_probe_pos<NEAREST>(g);
     const float3 X = ray_X(), w = ray_w();
     Seg s;
     seg_setup(s, make_float3(X.x - O.x, X.y - O.y, X.z - O.z), w, CF(kSegA), b, g.N);
@@ -391,7 +399,40 @@ __device__ __forceinline__ void decide(const GridDev& g, Lane& L, Stats<COUNT>& 
     }
 }
 
+// Traversal for fewer than 8 probes (Sec. 4.3): every probe, nearest to the
+// eye first (squared distances, ties to the lower index, the same arithmetic
+// as the loop-nest engine), as one pseudo-cell over [0, inf).
+__device__ __forceinline__ void nearest_start(const GridDev& g, float3 X) {
+    const int P = g.nx * g.ny * g.nz;  // <= 8, checked at grid creation
+    float d2[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        float3 O = probe_pos(g, k < P ? k : 0);
+        float dx = __fsub_rn(X.x, O.x), dy = __fsub_rn(X.y, O.y), dz = __fsub_rn(X.z, O.z);
+        d2[k] = k < P ? __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) : kInf;
+    }
+    unsigned used = 0, order = 0;
+    for (int q = 0; q < P; ++q) {
+        int pick = -1;
+        float best = kInf;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (!(used >> k & 1u) && k < P && (pick < 0 || d2[k] < best)) {
+                best = d2[k];
+                pick = k;
+            }
+        used |= 1u << pick;
+        order |= (unsigned)pick << (3 * q);
+    }
+    CI(kOrder) = (int)order;
+    CI(kQ) = 0;
+    CI(kCbits) = 0x100;  // the one pseudo-cell is the last
+    CF(kTin) = 0.0f;
+    CF(kTout) = kInf;
+}
+
 // Start the ray of slot `slot` (0..31) of 8x4 ray tile `tile`.
+template <bool NEAREST>
 __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb, int tile, int slot, Lane& L) {
     int lo = 0, hi = vb.n - 1;
     while (lo < hi) {
@@ -444,6 +485,11 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
         L.mode = kRayDone;
         return;
     }
+    if (NEAREST) {
+        nearest_start(g, X);
+        L.mode = kProbeStart;
+        return;
+    }
     L.mode = ray_enter_grid(g, X, w) ? kCellStart : kRayDone;
 }
 
@@ -473,9 +519,10 @@ __device__ __forceinline__ void write_ray(const GridDev& g, const OutDev& out, c
 // its 32 lanes busy, one texel visit per lane per iteration. COUNT selects
 // the instrumented variant (fetch counters and the max_steps cap); the plain
 // variant carries neither, which keeps the per-visit path short.
-template <int RADF, int NRMF, bool COUNT, int OCC>
+template <int RADF, int NRMF, bool COUNT, int OCC, bool NEAREST>
 __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream_kernel(GridDev g, ViewBatch vb,
                                                                                      OutDev out, unsigned* queue) {
+    const int n_probes = g.nx * g.ny * g.nz;  // nearest-probe traversal: probes per ray
     const int lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
     Lane L;
@@ -495,7 +542,7 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
             write_ray<RADF>(g, out, L);
             if (COUNT) {
                 const int cls = CI(kCls);
-                const bool eye = cls == kHit && cells == 0;  // eye-aligned lookup
+                const bool eye = cls == kHit && probes == 0;  // eye-aligned lookup
                 acc[0] += st.coarse;
                 acc[1] += st.fine;
                 acc[2] += st.normal;
@@ -525,8 +572,9 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
             int rank = __popc(idle & lanes_below);
             if (L.mode == kIdle && rank < avail) {
                 st = Stats<COUNT>();
-                cells = probes = 0;
-                start_ray(g, vb, pool_tile, pool_next + rank, L);  // kRayDone rays are written next round
+                cells = NEAREST ? 1 : 0;
+                probes = 0;
+                start_ray<NEAREST>(g, vb, pool_tile, pool_next + rank, L);  // kRayDone rays are written next round
             }
             pool_next += min(__popc(idle), avail);
             idle = __ballot_sync(kFull, L.mode == kIdle);
@@ -536,7 +584,13 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
 
         if (L.mode == kSegEnd) {  // MISS on this segment: next segment, or the probe is a MISS
             if (CI(kSegFinal)) {
-                L.mode = kNextCell;
+                if (NEAREST) {  // a MISS falls through to the next probe too
+                    const int q = CI(kQ) + 1;
+                    CI(kQ) = q;
+                    L.mode = q == n_probes ? kNextCell : kProbeStart;
+                } else {
+                    L.mode = kNextCell;
+                }
             } else {
                 CI(kSegI) += 1;
                 CF(kSegA) = CF(kSegB);
@@ -546,7 +600,10 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
         if (L.mode == kUnknownRes) {  // UNKNOWN falls through to the next probe of the cage
             const int q = CI(kQ) + 1;
             CI(kQ) = q;
-            if (q == 8) {
+            if (NEAREST) {  // any UNKNOWN makes an undecided ray UNKNOWN
+                CI(kCbits) |= 0x200;
+                L.mode = q == n_probes ? kNextCell : kProbeStart;
+            } else if (q == 8) {
                 CI(kCbits) |= 0x200;  // saw UNKNOWN
                 L.mode = kNextCell;
             } else {
@@ -575,11 +632,11 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
         }
         if (L.mode == kProbeStart) {
             ++probes;
-            probe_start(g, L);
+            probe_start<NEAREST>(g, L);
             L.mode = kSegStart;
         }
         if (L.mode == kSegStart) {
-            seg_start(g, L);
+            seg_start<NEAREST>(g, L);
             L.mode = kWalk;
         }
 
@@ -607,12 +664,19 @@ template <int RADF, int NRMF>
 cudaError_t launch_stream_fmt(const GridDev& g, const ViewBatch& vb, const OutDev& out, unsigned* queue, int blocks,
                               int occ, cudaStream_t s) {
     // the instrumented variant (counters, step cap) always uses the 64-register budget
-    if (out.counters || g.max_steps > 0)
-        render_stream_kernel<RADF, NRMF, true, 0><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
-    else if (occ == 1)
-        render_stream_kernel<RADF, NRMF, false, 1><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
-    else
-        render_stream_kernel<RADF, NRMF, false, 0><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+    const bool instr = out.counters || g.max_steps > 0;
+    if (g.nearest_probes) {
+        if (instr)
+            render_stream_kernel<RADF, NRMF, true, 0, true><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+        else
+            render_stream_kernel<RADF, NRMF, false, 0, true><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+    } else if (instr) {
+        render_stream_kernel<RADF, NRMF, true, 0, false><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+    } else if (occ == 1) {
+        render_stream_kernel<RADF, NRMF, false, 1, false><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+    } else {
+        render_stream_kernel<RADF, NRMF, false, 0, false><<<blocks, kStreamThreads, 0, s>>>(g, vb, out, queue);
+    }
     return cudaGetLastError();
 }
 
@@ -620,9 +684,11 @@ template <int RADF, int NRMF>
 int blocks_fmt(int occ) {
     int n = 0;
     if (occ == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<RADF, NRMF, false, 1>, kStreamThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<RADF, NRMF, false, 1, false>,
+                                                      kStreamThreads, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<RADF, NRMF, false, 0>, kStreamThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_stream_kernel<RADF, NRMF, false, 0, false>,
+                                                      kStreamThreads, 0);
     return n;
 }
 

@@ -432,8 +432,8 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             float3 O = probe_pos(g, k < P ? k : 0);
-            float dx = Xa[0] - O.x, dy = Xa[1] - O.y, dz = Xa[2] - O.z;
-            d2[k] = k < P ? dx * dx + dy * dy + dz * dz : kInf;
+            float dx = __fsub_rn(Xa[0], O.x), dy = __fsub_rn(Xa[1], O.y), dz = __fsub_rn(Xa[2], O.z);
+            d2[k] = k < P ? __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) : kInf;
         }
         unsigned used = 0;
         bool saw_unknown = false, step_limited = false;
