@@ -14,7 +14,7 @@ the host cores (cpu_baseline), fwd+adjoint ms/view on the differentiable-fit
 views, and SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lfp|reference]
-                  [--workload room|batched|fit|few|multiscale|build|sweep]
+                  [--workload room|batched|fit|few|multiscale|build|sweep|complexity]
 (few: four probes, the nearest-probe traversal Sec. 4.3 gives for fewer than
 8 probes.)
 Under torchrun every rank renders its own copy of the workload (weak scaling,
@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lfp", choices=["lfp", "reference"])
     ap.add_argument("--workload", default="room",
-                    choices=["room", "batched", "fit", "few", "multiscale", "build", "sweep"])
+                    choices=["room", "batched", "fit", "few", "multiscale", "build", "sweep", "complexity"])
     ap.add_argument("--views", type=int, default=64, help="multiscale: number of views (64 in the configuration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -441,9 +441,9 @@ def run_reference(args):
         return run_reference_multiscale(args)
     if args.workload == "build":
         return run_reference_build(args)
-    if args.workload == "sweep":
-        print(json.dumps({"impl": "reference", "unavailable": "the resolution sweep is a study over probe "
-                          "settings, not a throughput workload; the oracle arms of room and build cover it"}))
+    if args.workload in ("sweep", "complexity"):
+        print(json.dumps({"impl": "reference", "unavailable": "a study over probe settings or scenes, not a "
+                          "throughput workload; the oracle arms of room and build cover it"}))
         return
     sc, views, d, n, r = build_workload(args.workload)
     o = oracle.Oracle(sc.grid, d, n, r, traversal=1 if args.workload == "few" else 0)
@@ -922,6 +922,56 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_complexity(args):
+    """Scene complexity (the paper's observation that frame time barely
+    depends on the scene): the room grid and view with 8, 80, 640 and 5120
+    primitives (80 % spheres), object sizes scaled by (80 / n)^(1/3) so the
+    occupied volume stays comparable; 80 is the room workload itself."""
+    import torch
+    import synth
+    import paper_2507_14624_gb300 as lfpk
+    from paper_2507_14624_gb300 import lfp
+    torch.cuda.set_device(dist_env()[2])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for n in (8, 80, 640, 5120):
+        g = synth.Grid(4, 4, 4, 0.5, 256, 16)
+        ns = int(round(0.8 * n))
+        sc = synth.make_scene(g, ns, n - ns, [0.7, 0.3], seed=2, accel_cell=0.25, size_scale=(80.0 / n) ** (1 / 3))
+        v = synth.random_view(sc, 102, 1920, 1080, 70.0)
+        d, nn, r = sc.probe_maps()
+        grid = lfpk.ProbeGrid(g)
+        grid.upload(d, nn, r)
+        c = grid.render([v], aux=False, counters=True)["counters"].cpu().tolist()
+        cls = grid.render([v], aux=False)["cls"]
+        ms = 0.0
+        for k in range(args.warmup + args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            grid.render([v], aux=False)
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ms += e0.elapsed_time(e1)
+        ms /= args.steps
+        rays = v.W * v.H
+        rows.append({"primitives": n, "ms_per_frame": round(ms, 4), "mrays_per_s": round(rays / ms / 1e3, 1),
+                     "hit": round(float((cls == 1).float().mean().item()), 4),
+                     "low_res_visits_per_ray": round(c[0] / rays, 2), "full_res_visits_per_ray": round(c[1] / rays, 2),
+                     "probes_per_ray": round(c[5] / rays, 3)})
+        grid.close()
+    line = {"metric": "Mrays/s at 1080p vs scene primitives (room grid, N=256)", "value": rows[-1]["mrays_per_s"],
+            "unit": "Mrays/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "f32", "data": "synthetic (seeded room scenes of 8..5120 primitives, probe maps ray-cast)",
+            "config": {"workload": "complexity: room grid 4x4x4 spacing 0.5, N=256 M=16, 1 view 1920x1080; "
+                                   "8/80/640/5120 primitives", "value_is": "5120 primitives",
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "complexity": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_fit(args):
     """Differentiable fit: the room grid (seed 4), 64 views of 800x800, targets
     = ground-truth render + N(0, 0.01^2); radiance re-initialised U[0,1]; L2
@@ -973,6 +1023,8 @@ if __name__ == "__main__":
         run_build(a)
     elif a.workload == "sweep" and a.impl != "reference":
         run_sweep(a)
+    elif a.workload == "complexity" and a.impl != "reference":
+        run_complexity(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

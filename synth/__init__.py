@@ -262,7 +262,7 @@ def _build_accel(spheres: np.ndarray, boxes: np.ndarray, room: np.ndarray, cell:
 
 def make_scene(grid: Grid, n_spheres: int, n_boxes: int, light_intensities, seed: int,
                ambient: float = 0.1, room_margin: float | None = None, clearance: float = 0.02,
-               accel_cell: float | None = None) -> Scene:
+               accel_cell: float | None = None, size_scale: float = 1.0) -> Scene:
     """Random scene around a probe grid.
 
     * Room: the grid's bounding box grown by half a spacing on each side,
@@ -273,6 +273,8 @@ def make_scene(grid: Grid, n_spheres: int, n_boxes: int, light_intensities, seed
     * Objects are redrawn while one contains a probe or comes within
       `clearance` of one. Albedo U[0,1]^3.
     * Lights: directions uniform on the upper hemisphere.
+    * size_scale multiplies every radius and half-extent (denser scenes of
+      smaller objects).
     """
     rng = SplitMix64(seed)
     margin = 0.5 * grid.spacing if room_margin is None else room_margin
@@ -292,7 +294,7 @@ def make_scene(grid: Grid, n_spheres: int, n_boxes: int, light_intensities, seed
 
     spheres = []
     while len(spheres) < n_spheres:
-        r = rng.uniform(0.05, 0.2)
+        r = rng.uniform(0.05, 0.2) * size_scale
         c = np.array([rng.uniform(room[a], room[a + 3]) for a in range(3)])
         alb = [rng.uniform() for _ in range(3)]
         if far_from_probes_sphere(c, r):
@@ -301,7 +303,7 @@ def make_scene(grid: Grid, n_spheres: int, n_boxes: int, light_intensities, seed
     scale = grid.spacing / 0.5
     cap = 0.4 * grid.spacing
     while len(boxes) < n_boxes:
-        h = np.array([min(rng.uniform(0.05, 0.25) * scale, cap) for _ in range(3)])
+        h = np.array([min(rng.uniform(0.05, 0.25) * scale, cap) * size_scale for _ in range(3)])
         c = np.array([rng.uniform(room[a], room[a + 3]) for a in range(3)])
         alb = [rng.uniform() for _ in range(3)]
         b = np.array([*(c - h), *(c + h)])

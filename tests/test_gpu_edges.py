@@ -128,3 +128,19 @@ def test_8k_view_sampled():
     idx = torch.tensor(pix, device="cuda")
     sl = {k: t[idx] for k, t in out.items()}
     _check(sl, oracle.Oracle(sc.grid, d, n, r).render(v, pix), sc.grid.N, len(pix))
+
+
+@pytest.mark.parametrize("n", [640, 5120])
+def test_dense_scenes(n):
+    """The scene-complexity workload's denser scenes (80 % spheres, sizes
+    scaled by (80 / n)^(1/3)): full 480x270 frames against the oracle. With
+    5120 small objects the probes see little beyond their neighbourhood and
+    almost every pixel is UNKNOWN; the classes must still match."""
+    g = synth.Grid(4, 4, 4, 0.5, 256, 16)
+    ns = int(round(0.8 * n))
+    sc = synth.make_scene(g, ns, n - ns, [0.7, 0.3], seed=2, accel_cell=0.25, size_scale=(80.0 / n) ** (1 / 3))
+    v = synth.random_view(sc, 102, 480, 270, 70.0)
+    d, nn, r = sc.probe_maps()
+    grid = _grid(g, d, nn, r)
+    out = grid.render([v], hit_texel=True)
+    _check(out, oracle.Oracle(g, d, nn, r).render(v), g.N, v.n_pixels)
