@@ -213,10 +213,13 @@ lfp_status lfp_autotune(lfp_grid* grid, const lfp_view* views, int n_views,
 lfp_status lfp_render_to_host(lfp_grid* grid, const lfp_view* views, int n_views,
                               float* rgb_host, uint8_t* cls_host, void* cuda_stream);
 
-/* Frame-loop form of lfp_render_to_host: renders on `cuda_stream` into one
- * of two grid-owned device buffers (used in turn) and queues the copy of
- * rgb / cls to the host buffers on a grid-owned copy stream, then returns
- * without waiting, so the copy of one call overlaps the render of the next.
+/* Frame-loop form of lfp_render_to_host: renders into one of two grid-owned
+ * device buffers (used in turn), each on its own grid-owned stream that
+ * first waits for the work queued so far on `cuda_stream`, and queues the
+ * copy of rgb / cls to the host buffers on a grid-owned copy stream; returns
+ * without waiting. The copy of one call and the end of its render overlap
+ * the render of the next. Later work on `cuda_stream` does not wait for
+ * these renders; lfp_sync_host does.
  * Copies run in call order. The host buffers of a call hold its result
  * once lfp_sync_host(grid) has returned (read them only then). Pinned host
  * memory is needed for the overlap. */

@@ -43,6 +43,9 @@ struct lfp_grid {
     long long async_pixels = 0;
     int async_slot = 0;
     cudaStream_t copy_stream = nullptr;
+    cudaStream_t render_stream[2] = {nullptr, nullptr};  // one per buffer: consecutive frames overlap
+    unsigned* async_queue = nullptr;                     // a work-queue head per render stream
+    cudaEvent_t issued[2] = {nullptr, nullptr};          // the caller's stream reached the call
     cudaEvent_t rendered[2] = {nullptr, nullptr};
     cudaEvent_t copied[2] = {nullptr, nullptr};
     std::vector<unsigned char> uploaded;
@@ -191,7 +194,8 @@ bool valid_tile(int w, int h) {
 }
 
 lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const OutDev& out,
-                       const lfp_render_opts* opts, cudaStream_t s) {
+                       const lfp_render_opts* opts, cudaStream_t s, unsigned* queue = nullptr) {
+    if (!queue) queue = g->tile_counter;  // the persistent launches' work-queue head
     int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0, engine = g->engine, occ = g->stream_occ;
     if (opts) {
         if (opts->engine < LFP_ENGINE_AUTO || opts->engine > LFP_ENGINE_NESTED) return LFP_ERR_INVALID_ARG;
@@ -232,8 +236,8 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
             }
             vb.total_tiles = (int)tiles;
             int blocks = (int)std::min<long long>(g->stream_blocks[occ], (tiles + 3) / 4);
-            LFP_CUDA(cudaMemsetAsync(g->tile_counter, 0, sizeof(unsigned), s));
-            LFP_CUDA(launch_render_stream(gd, g->desc.radiance_fmt, g->desc.normal_fmt, vb, out, g->tile_counter,
+            LFP_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
+            LFP_CUDA(launch_render_stream(gd, g->desc.radiance_fmt, g->desc.normal_fmt, vb, out, queue,
                                           blocks, occ, s));
         }
         return LFP_OK;
@@ -241,7 +245,7 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
     RenderLaunch L;
     L.flat = flat;
     L.persistent = sched == LFP_SCHED_PERSISTENT;
-    L.tile_counter = g->tile_counter;
+    L.tile_counter = queue;
     L.persistent_blocks = 0;
     if (L.persistent) {
         int per_sm = render_max_active_blocks(g->desc.radiance_fmt, g->desc.normal_fmt, tw * th);
@@ -260,7 +264,7 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
             if (tiles > (1LL << 31) - 1) return LFP_ERR_INVALID_ARG;
         }
         vb.total_tiles = (int)tiles;
-        if (L.persistent) LFP_CUDA(cudaMemsetAsync(g->tile_counter, 0, sizeof(unsigned), s));
+        if (L.persistent) LFP_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
         LFP_CUDA(launch_render(gd, g->desc.radiance_fmt, g->desc.normal_fmt, vb, out, L, s));
     }
     return LFP_OK;
@@ -286,7 +290,10 @@ void destroy(lfp_grid* g) {
         dev_free(g->async_cls[k]);
         if (g->rendered[k]) cudaEventDestroy(g->rendered[k]);
         if (g->copied[k]) cudaEventDestroy(g->copied[k]);
+        if (g->issued[k]) cudaEventDestroy(g->issued[k]);
+        if (g->render_stream[k]) cudaStreamDestroy(g->render_stream[k]);
     }
+    dev_free(g->async_queue);
     if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     delete g;
 }
@@ -652,8 +659,11 @@ lfp_status lfp_render_to_host_async(lfp_grid* g, const lfp_view* views, int n_vi
     if (!dg.ok) return LFP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     if (!g->copy_stream) {
+        LFP_TRY(dev_alloc((void**)&g->async_queue, 2 * sizeof(unsigned)));
         LFP_CUDA(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
         for (int k = 0; k < 2; ++k) {
+            LFP_CUDA(cudaStreamCreateWithFlags(&g->render_stream[k], cudaStreamNonBlocking));
+            LFP_CUDA(cudaEventCreateWithFlags(&g->issued[k], cudaEventDisableTiming));
             LFP_CUDA(cudaEventCreateWithFlags(&g->rendered[k], cudaEventDisableTiming));
             LFP_CUDA(cudaEventCreateWithFlags(&g->copied[k], cudaEventDisableTiming));
         }
@@ -663,6 +673,8 @@ lfp_status lfp_render_to_host_async(lfp_grid* g, const lfp_view* views, int n_vi
         total = std::max(total, views[i].out_offset + (long long)views[i].W * views[i].H);
     if (total > g->async_pixels) {  // grow both buffers once nothing uses them
         LFP_CUDA(cudaStreamSynchronize(g->copy_stream));
+        LFP_CUDA(cudaStreamSynchronize(g->render_stream[0]));
+        LFP_CUDA(cudaStreamSynchronize(g->render_stream[1]));
         LFP_CUDA(cudaStreamSynchronize(s));
         for (int k = 0; k < 2; ++k) {
             dev_free(g->async_rgb[k]);
@@ -679,14 +691,19 @@ lfp_status lfp_render_to_host_async(lfp_grid* g, const lfp_view* views, int n_vi
     }
     const int k = g->async_slot;
     g->async_slot ^= 1;
-    // the buffer's previous copy (two calls ago) must be out before it is reused
-    LFP_CUDA(cudaStreamWaitEvent(s, g->copied[k], 0));
+    // render k runs on its own stream after the caller's stream work so far
+    // and after the buffer's previous copy (two calls ago); the other render
+    // stream's frame may still be finishing, so consecutive frames overlap
+    cudaStream_t rs = g->render_stream[k];
+    LFP_CUDA(cudaEventRecord(g->issued[k], s));
+    LFP_CUDA(cudaStreamWaitEvent(rs, g->issued[k], 0));
+    LFP_CUDA(cudaStreamWaitEvent(rs, g->copied[k], 0));
     OutDev out;
     std::memset(&out, 0, sizeof(out));
     out.rgb = g->async_rgb[k];
     out.cls = g->async_cls[k];
-    LFP_TRY(render_impl(g, views, n_views, out, nullptr, s));
-    LFP_CUDA(cudaEventRecord(g->rendered[k], s));
+    LFP_TRY(render_impl(g, views, n_views, out, nullptr, rs, g->async_queue + k));
+    LFP_CUDA(cudaEventRecord(g->rendered[k], rs));
     LFP_CUDA(cudaStreamWaitEvent(g->copy_stream, g->rendered[k], 0));
     if (rgb_host)
         LFP_CUDA(cudaMemcpyAsync(rgb_host, g->async_rgb[k], total * 12, cudaMemcpyDeviceToHost, g->copy_stream));
