@@ -18,9 +18,16 @@
  *     octahedral map gives at most 4 segments; low-resolution tracing tests
  *     distance only; high-resolution tracing adds the normal test, HIT /
  *     UNKNOWN; eye aligned with a probe is an O(1) lookup.
- *   - Sec. 4.3 (Ray Trace Using Multiple Probes): grid iterator over cubes.
+ *   - Sec. 4.3 (Ray Trace Using Multiple Probes): grid iterator over cubes;
+ *     the traversal for fewer than 8 probes (orc_trace_ray, traversal 1).
+ *   - Sec. 4.1 and 5.1 (simulated probe data, probe data generation): probe
+ *     maps from a point cloud, nearest point per texel (orc_splat_probes).
  *   - Appendix A, Algorithms RayMarching, traceOneProbe, traceOneRaySegment,
  *     lowResolutionTracing, highResolutionTracing.
+ *
+ * Every function is pinned by the CPU tests in tests/test_oracle_*.py
+ * against closed forms, brute force, invariants or the analytic scene (see
+ * each test's docstring); none is marked "parity unpinned".
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   R1 octahedral pole +z; texel (i, j) covers u in [i/N, (i+1)/N) of
