@@ -96,8 +96,11 @@ __global__ void backward_kernel(int N, PixBatch pb, const float* __restrict__ gr
 }
 
 // Warp-aggregated adjoint: pixels of one warp that hit the same texel (the
-// maps are magnified: hundreds of pixels per texel at 1080p) are summed with
-// shuffles and written by one atomic per distinct texel and channel.
+// maps are magnified: hundreds of pixels per texel at 1080p) are summed and
+// written by one atomic per texel and channel. A warp holds 32 consecutive
+// pixels of a row, so equal texels come in runs of neighbouring lanes: a
+// segmented sum over the runs (five shuffle steps) leaves each run's total
+// in its last lane, which does the atomics.
 __global__ void backward_warp_kernel(int N, PixBatch pb, const float* __restrict__ grad_rgb,
                                      const uint8_t* __restrict__ cls, const int32_t* __restrict__ aux_probe,
                                      const float* __restrict__ aux_uv, float* __restrict__ grad_rad) {
@@ -131,32 +134,31 @@ __global__ void backward_warp_kernel(int N, PixBatch pb, const float* __restrict
             g1 = grad_rgb[3 * o + 1];
             g2 = grad_rgb[3 * o + 2];
         }
+        if (__ballot_sync(full, hit) == 0u) continue;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            unsigned long long key = hit ? (unsigned long long)p * NN + (unsigned long long)idx[k] : ~0ull;
-            float vx = w[k] * g0, vy = w[k] * g1, vz = w[k] * g2;
-            unsigned todo = __ballot_sync(full, hit);
-            while (todo) {
-                int src = __ffs(todo) - 1;
-                unsigned long long kk = __shfl_sync(full, key, src);
-                bool mine = hit && key == kk;
-                unsigned grp = __ballot_sync(full, mine);
-                float sx = mine ? vx : 0.f, sy = mine ? vy : 0.f, sz = mine ? vz : 0.f;
-                if (__popc(grp) > 1) {
+            const unsigned long long key = hit ? (unsigned long long)p * NN + (unsigned long long)idx[k] : ~0ull;
+            float sx = w[k] * g0, sy = w[k] * g1, sz = w[k] * g2;
+            const unsigned long long prev = __shfl_up_sync(full, key, 1);
+            const unsigned long long next = __shfl_down_sync(full, key, 1);
+            const unsigned heads = __ballot_sync(full, lane == 0 || key != prev);
+            const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of my run
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        sx += __shfl_xor_sync(full, sx, off);
-                        sy += __shfl_xor_sync(full, sy, off);
-                        sz += __shfl_xor_sync(full, sz, off);
-                    }
+            for (int off = 1; off < 32; off <<= 1) {
+                const float tx = __shfl_up_sync(full, sx, off);
+                const float ty = __shfl_up_sync(full, sy, off);
+                const float tz = __shfl_up_sync(full, sz, off);
+                if (lane - off >= start) {
+                    sx += tx;
+                    sy += ty;
+                    sz += tz;
                 }
-                if (lane == src) {
-                    float* t = grad_rad + 3 * kk;
-                    atomicAdd(t + 0, sx);
-                    atomicAdd(t + 1, sy);
-                    atomicAdd(t + 2, sz);
-                }
-                todo &= ~grp;
+            }
+            if (hit && (lane == 31 || next != key)) {  // last lane of a run
+                float* t = grad_rad + 3 * key;
+                atomicAdd(t + 0, sx);
+                atomicAdd(t + 1, sy);
+                atomicAdd(t + 2, sz);
             }
         }
     }
