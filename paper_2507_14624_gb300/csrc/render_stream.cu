@@ -357,6 +357,17 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
         L.lo1 = L.j * k;
         L.hi1 = L.lo1 + k - 1;
         L.u1 = ue;
+        {  // skip the full-resolution texels the ray passes in front of dmin (fine_start)
+            Seg s;
+            s.A1 = L.A1;
+            s.A2 = L.A2;
+            s.e = L.e;
+            const float us = fine_start(s, d2, L.u, L.Pa - d2 * L.D2a, ue, Pb - d2 * D2b);
+            const float Ds = fmaf(-L.e, us, 1.0f);
+            L.Pa = fmaf(fmaf(L.A2, us, L.A1), us, L.A0);
+            L.D2a = Ds * Ds;
+            L.u = us;
+        }
         L.i = min(max(texel_of(fmaf(CF(kK0), L.u, CF(kP00)), N, L.dir0), L.lo0), L.hi0);
         L.j = min(max(texel_of(fmaf(CF(kK1), L.u, CF(kP01)), N, L.dir1), L.lo1), L.hi1);
         L.ux = L.dir0 == 0 ? kInf : fmaxf(fmaf((float)(L.dir0 > 0 ? L.i + 1 : L.i), L.m0, L.q0), L.u);

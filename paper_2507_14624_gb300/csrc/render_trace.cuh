@@ -159,6 +159,29 @@ struct Stats {
     unsigned coarse = 0, fine = 0, normal = 0, steps = 0;
 };
 
+// Where the full-resolution walk under a candidate low-resolution texel
+// [u0, u1] can start: until the ray's radial distance first reaches the
+// block's minimum dmin (d2 = dmin^2) every full-resolution texel is in front
+// of its stored surface. f(u) = |Ya + u V|^2 - d2 (1 - e u)^2 is quadratic
+// with f0 = f(u0) < 0 <= f1 = f(u1) when there is anything to skip; the
+// estimate of its root never lies beyond it: the chord's zero when f is
+// convex, the zero of the tangent at u0 when f is concave, then shortened by
+// 1/256 of the skipped length to cover rounding.
+__device__ __forceinline__ float fine_start(const Seg& s, float d2, float u0, float f0, float u1, float f1) {
+    if (!(f0 < 0.0f) || !(f1 >= 0.0f) || !(u1 > u0)) return u0;
+    const float a = s.A2 - d2 * s.e * s.e;
+    float us;
+    if (a >= 0.0f) {
+        us = fmaf(u1 - u0, __fdividef(-f0, f1 - f0), u0);
+    } else {
+        const float fp = fmaf(2.0f * a, u0, fmaf(2.0f * d2, s.e, s.A1));
+        if (!(fp > 0.0f)) return u0;
+        us = u0 - __fdividef(f0, fp);
+    }
+    us = fmaf(us - u0, 255.0f / 256.0f, u0);
+    return fminf(fmaxf(us, u0), u1);
+}
+
 // highResolutionTracing over full-resolution texels inside the index box
 // [lo, hi] for u in [u0, u1]. P0, D20: |Ya + u0 V|^2 and (1 - e u0)^2.
 // Returns true when a decision was reached.
@@ -257,8 +280,10 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
                     return true;
                 }
             }
-            if (fine_walk<NRMF, COUNT>(g, s, pbase, u, ue, Pa, D2a, I * k, J * k, I * k + k - 1, J * k + k - 1, out,
-                                       st, step_limited))
+            const float us = fine_start(s, d2, u, Pa - d2 * D2a, ue, Pb - d2 * D2b);
+            const float Ds = fmaf(-s.e, us, 1.0f);
+            if (fine_walk<NRMF, COUNT>(g, s, pbase, us, ue, fmaf(fmaf(s.A2, us, s.A1), us, s.A0), Ds * Ds, I * k, J * k,
+                                       I * k + k - 1, J * k + k - 1, out, st, step_limited))
                 return true;
         }
         if (last) return false;
