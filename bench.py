@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Mrays/s at 1080p (fwd) and fwd+adjoint ms/view; % of HBM/L2 roofline"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
+OCCUPANCY = {"8": 1, "9": 2}  # --occupancy -> LFP_OCC_8 / LFP_OCC_9
 
 
 def parse():
@@ -50,6 +51,10 @@ def parse():
     ap.add_argument("--views", type=int, default=64, help="multiscale: number of views (64 in the configuration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--occupancy", default="auto", choices=["auto", "8", "9"],
+                    help="batched / multiscale: the autotuner's launch configuration (default), or the streaming "
+                         "engine pinned to 8 blocks per SM (64 registers) or 9 (56 registers); the pinned forms "
+                         "are what the per-kernel ncu counts are taken on")
     return ap.parse_args()
 
 
@@ -138,31 +143,49 @@ def render_source_sha(workload="room"):
     return h.hexdigest()[:16]
 
 
-def ncu_summary(workload):
+def ncu_summary(workload, occ=None):
     """The committed ncu summary of the render kernel for this workload, if it
-    was taken on the current kernel source; else an empty dict."""
+    was taken on the current kernel source; else an empty dict. Summaries
+    taken per register budget of the streaming engine keep them under
+    "by_occupancy"; `occ` ("8" or "9") selects one."""
     p = os.path.join(ROOT, "profiles", f"render_{workload}_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         if d.get("source_sha") == render_source_sha(workload):
+            if "by_occupancy" in d:
+                return d["by_occupancy"].get(occ, {}) if occ else {}
             return d
     except Exception:
         pass
     return {}
 
 
-def ncu_traffic(workload):
+def occupancy_key(pinned, tuned):
+    """"8" / "9": the streaming engine's register budget a launch ran with
+    (pinned, or picked by the autotuner; 8 when neither); None for the
+    loop-nest engine."""
+    if pinned != "auto":
+        return pinned
+    if not tuned:
+        return "8"
+    if tuned.get("engine") != 1:  # LFP_ENGINE_STREAM
+        return None
+    return "9" if tuned.get("occupancy") == 2 else "8"  # LFP_OCC_9
+
+
+def ncu_traffic(workload, occ=None):
     """DRAM bytes per launch (read + write) from the committed ncu summary, or None."""
-    d = ncu_summary(workload)
+    d = ncu_summary(workload, occ)
     return float(d["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in d else None
 
 
-def issue_roofline(workload, ms_launch, sm_mhz, n_sm):
+def issue_roofline(workload, ms_launch, sm_mhz, n_sm, occ=None):
     """The kernel is bound by instruction issue: warp instructions per launch
-    (an ncu count on the current source) over the event-timed launch, against
-    n_sm x 4 schedulers x one warp instruction per clock."""
-    d = ncu_summary(workload)
+    (an ncu count on the current source and register budget) over the
+    event-timed launch, against n_sm x 4 schedulers x one warp instruction per
+    clock."""
+    d = ncu_summary(workload, occ)
     if "warp_inst_per_launch" not in d or not sm_mhz:
         return None
     achieved = d["warp_inst_per_launch"] / (ms_launch / 1e3) / 1e9
@@ -223,9 +246,14 @@ def run_lfp(args):
     grid.upload(d, n, r)
     sched = lfpk.LFP_SCHED_PERSISTENT if len(views) > 1 else 0
     tuned = None
-    if len(views) > 1:  # the batched form: launch configuration picked by the autotuner
+    pin_engine, pin_occ = 0, 0  # 0: the grid's default (autotuned for the batched form)
+    if args.occupancy != "auto":
+        pin_engine, pin_occ = lfpk.LFP_ENGINE_STREAM, OCCUPANCY[args.occupancy]
+        sched = 0
+    elif len(views) > 1:  # the batched form: launch configuration picked by the autotuner
         tuned = grid.autotune(views)
         sched = 0
+    occ_key = occupancy_key(args.occupancy, tuned)
     arr, nv, total = lfpk.make_views(views)
     dev = torch.device("cuda", local)
     rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
@@ -234,6 +262,7 @@ def run_lfp(args):
     outs.rgb, outs.cls = rgb.data_ptr(), cls.data_ptr()
     opts = lfp.lfp_render_opts()
     opts.schedule = sched
+    opts.engine, opts.occupancy = pin_engine, pin_occ
     stream = torch.cuda.current_stream()
     sh = lfpk._stream_handle(stream)
     launches_per_step = (nv + 127) // 128
@@ -243,7 +272,7 @@ def run_lfp(args):
 
     graph = None
     if len(views) > 1:  # the batched form: one persistent launch replayed from a CUDA graph
-        graph, gout = grid.render_graph(views, aux=False)
+        graph, gout = grid.render_graph(views, aux=False, engine=pin_engine, occupancy=pin_occ)
         rgb, cls = gout["rgb"], gout["cls"]
         outs.rgb, outs.cls = rgb.data_ptr(), cls.data_ptr()
 
@@ -305,13 +334,13 @@ def run_lfp(args):
 
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (ms_launch / 1e3) / 1e9
-    traffic = ncu_traffic(args.workload)
+    traffic = ncu_traffic(args.workload, occ_key)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": kernel_of(args.workload),
                 "counters_per_launch": counters,
                 "issue": issue_roofline(args.workload, ms_launch, clk.get("sm_mhz"),
-                                        torch.cuda.get_device_properties(dev).multi_processor_count)}
+                                        torch.cuda.get_device_properties(dev).multi_processor_count, occ_key)}
 
     extra = {}
     if not args.no_adjoint and rank == 0:
@@ -329,7 +358,7 @@ def run_lfp(args):
                 "dtype": "f16+f32" if f16 else "f32", "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
                 "config": workload_info(args.workload, views, sc.grid), "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "cuda_graph": graph is not None,
-                "autotuned": tuned,
+                "autotuned": tuned, "occupancy": args.occupancy if args.occupancy != "auto" else occ_key,
                 "roofline": roofline, "clocks": clk,
                 "cpu_baseline": cpu, **extra}
         print(json.dumps(line), flush=True)
@@ -508,16 +537,21 @@ def run_multiscale(args):
     lev = h.level_of(views)
     launches_per_step = len(set(lev))
     tuned = {}
+    pin_engine, pin_occ = 0, 0  # 0: each level's default (autotuned)
+    if args.occupancy != "auto":
+        pin_engine, pin_occ = lfpk.LFP_ENGINE_STREAM, OCCUPANCY[args.occupancy]
     for k, g in enumerate(h.grids):  # each level's launch configuration from the autotuner
         mine = [v for v, l in zip(views, lev) if l == k]
-        if mine:
+        if mine and args.occupancy == "auto":
             tuned[str(k)] = g.autotune(mine)
-    graph, out = h.render_graph(views, aux=False)
+    graph, out = h.render_graph(views, aux=False, engine=pin_engine, occupancy=pin_occ)
 
     cnt = torch.zeros(lfp.N_COUNTERS, dtype=torch.int64, device=dev)
     oc = lfp.lfp_outputs()
     oc.rgb, oc.cls, oc.counters = out["rgb"].data_ptr(), out["cls"].data_ptr(), cnt.data_ptr()
-    lfp.lfp_render_levels(h.handles, arr, nv, oc, None, lfpk._stream_handle(stream))
+    copts = lfp.lfp_render_opts()
+    copts.engine, copts.occupancy = pin_engine, pin_occ
+    lfp.lfp_render_levels(h.handles, arr, nv, oc, copts, lfpk._stream_handle(stream))
     torch.cuda.synchronize()
     counters = dict(zip(lfp.COUNTER_NAMES, (int(x) for x in cnt.cpu().tolist())))
     alg_bytes = bytes_model(counters, True, True)
@@ -588,22 +622,34 @@ def run_multiscale(args):
 
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
-    # ncu counts were taken on a 9-view run of the same levels (per ray, scaled
-    # to this step's rays); per launch = per step / launches
-    summ = ncu_summary("multiscale")
-    traffic = summ["dram_bytes_per_ray"] * total / launches_per_step if "dram_bytes_per_ray" in summ else None
+    # ncu counts were taken per level and register budget on a 9-view run of
+    # the same levels (per ray, scaled to this step's rays of each level, with
+    # the budget each level ran with); per launch = per step / launches
+    summ = ncu_summary("multiscale").get("levels", {})
+    kernels, inst, dram = {}, 0.0, 0.0
+    for k in sorted(set(lev)):
+        rays_k = sum(v.W * v.H for v, l in zip(views, lev) if l == k)
+        occ_k = occupancy_key(args.occupancy, tuned.get(str(k)))
+        kernels[str(k)] = f"render_stream_kernel ({occ_k} blocks/SM)" if occ_k else "render_kernel (loop nest)"
+        c = summ.get(str(k), {}).get("by_occupancy", {}).get(occ_k or "", {})
+        if inst is not None and "warp_inst_per_ray" in c:
+            inst += c["warp_inst_per_ray"] * rays_k
+            dram += c["dram_bytes_per_ray"] * rays_k
+        else:
+            inst = None  # a level without a count on this source and configuration
+    traffic = dram / launches_per_step if inst is not None else None
     issue = None
-    if "warp_inst_per_ray" in summ and clk.get("sm_mhz"):
+    if inst is not None and clk.get("sm_mhz"):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        ach = summ["warp_inst_per_ray"] * total / (ms_step / 1e3) / 1e9
+        ach = inst / (ms_step / 1e3) / 1e9
         pk = n_sm * 4 * clk["sm_mhz"] / 1e3
         issue = {"achieved": round(ach, 1), "peak": round(pk, 1), "unit": "G warp-inst/s", "frac": round(ach / pk, 4),
-                 "warp_inst_per_ray": summ["warp_inst_per_ray"],
+                 "warp_inst_per_step": int(inst),
                  "peak_basis": f"{n_sm} SMs x 4 schedulers x {clk['sm_mhz']:.0f} MHz (median sampled SM clock)"}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None if traffic is None else round(traffic),
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": int(alg_bytes / launches_per_step),
-                "algorithmic_bytes_per_step": int(alg_bytes), "kernel": "render_stream_kernel",
+                "algorithmic_bytes_per_step": int(alg_bytes), "kernel": kernels,
                 "counters_per_step": counters, "issue": issue}
     cpu = None
     if want_cpu:

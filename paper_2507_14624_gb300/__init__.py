@@ -195,25 +195,29 @@ class ProbeGrid:
         b = lfp.lfp_autotune(self.handle, arr, n, o, _stream_handle(stream))
         return {"engine": b.engine, "tile": (b.tile_w, b.tile_h), "schedule": b.schedule, "occupancy": b.occupancy}
 
-    def render_graph(self, views, aux=False, stream=None):
+    def render_graph(self, views, aux=False, engine=0, occupancy=0, stream=None):
         """Capture one render of these views in a CUDA graph (outputs are
         preallocated and reused). Returns (graph, outputs); graph.replay()
-        re-renders into the same tensors."""
+        re-renders into the same tensors. engine / occupancy as in render
+        (0: the grid's default)."""
         import torch
         s = torch.cuda.Stream() if stream is None else stream
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            out = self.render(views, aux=aux, stream=s)  # warm-up outside capture
+            out = self.render(views, aux=aux, engine=engine, occupancy=occupancy, stream=s)  # warm-up outside capture
         torch.cuda.current_stream().wait_stream(s)
         arr, n, total = make_views(views)
         o = lfp.lfp_outputs()
         o.rgb, o.cls = out["rgb"].data_ptr(), out["cls"].data_ptr()
         o.aux_probe = out["probe"].data_ptr() if aux else None
         o.aux_uv = out["uv"].data_ptr() if aux else None
+        opts = lfp.lfp_render_opts()
+        opts.engine = engine
+        opts.occupancy = occupancy
         graph = torch.cuda.CUDAGraph()
-        keep = (arr, o)
+        keep = (arr, o, opts)
         with torch.cuda.graph(graph, stream=s):
-            lfp.lfp_render_ex(self.handle, arr, n, o, None, _stream_handle(s))
+            lfp.lfp_render_ex(self.handle, arr, n, o, opts, _stream_handle(s))
         graph._lfp_keep = keep
         return graph, out
 
@@ -286,32 +290,37 @@ class ProbeHierarchy:
         o.counters = out["counters"].data_ptr() if counters else None
         return out, o
 
-    def render(self, views, aux=True, hit_texel=False, counters=False, engine=0, stream=None):
+    def render(self, views, aux=True, hit_texel=False, counters=False, engine=0, occupancy=0, stream=None):
         """Like ProbeGrid.render; `probe` indexes the probes of each view's level."""
         arr, n, total = make_views(views)
         out, o = self._outputs(total, aux, hit_texel, counters)
         opts = lfp.lfp_render_opts()
         opts.engine = engine
+        opts.occupancy = occupancy
         lfp.lfp_render_levels(self.handles, arr, n, o, opts, _stream_handle(stream))
         return out
 
-    def render_graph(self, views, aux=False, stream=None):
-        """One hierarchy render captured in a CUDA graph (outputs reused)."""
+    def render_graph(self, views, aux=False, engine=0, occupancy=0, stream=None):
+        """One hierarchy render captured in a CUDA graph (outputs reused);
+        engine / occupancy as in render (0: each level's default)."""
         import torch
         s = torch.cuda.Stream() if stream is None else stream
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            out = self.render(views, aux=aux, stream=s)
+            out = self.render(views, aux=aux, engine=engine, occupancy=occupancy, stream=s)
         torch.cuda.current_stream().wait_stream(s)
         arr, n, total = make_views(views)
         o = lfp.lfp_outputs()
         o.rgb, o.cls = out["rgb"].data_ptr(), out["cls"].data_ptr()
         o.aux_probe = out["probe"].data_ptr() if aux else None
         o.aux_uv = out["uv"].data_ptr() if aux else None
+        opts = lfp.lfp_render_opts()
+        opts.engine = engine
+        opts.occupancy = occupancy
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=s):
-            lfp.lfp_render_levels(self.handles, arr, n, o, None, _stream_handle(s))
-        graph._lfp_keep = (arr, o)
+            lfp.lfp_render_levels(self.handles, arr, n, o, opts, _stream_handle(s))
+        graph._lfp_keep = (arr, o, opts)
         return graph, out
 
     def render_backward(self, views, grad_rgb, cls, probe, uv, grads=None, reduction=0, stream=None):

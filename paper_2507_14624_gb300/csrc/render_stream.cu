@@ -143,9 +143,10 @@ __device__ __forceinline__ void cell_start(const GridDev& g) {
         tm[a] = st == 0 ? kInf
                         : (grid_plane(og[a], g.spacing, c[a] + (st > 0 ? 1 : 0)) - Xa[a]) * frcp(Wa[a]);
     }
-    int ax = 0;
-    if (tm[1] < tm[ax]) ax = 1;
-    if (tm[2] < tm[ax]) ax = 2;
+    // first exit, ties to the lower axis; selects rather than a run-time
+    // index keep tm in registers (no stack frame)
+    int ax = tm[1] < tm[0] ? 1 : 0;
+    if (tm[2] < (ax ? tm[1] : tm[0])) ax = 2;
     int st = step_of(cbits, ax);
     int cax = ax == 0 ? c[0] : (ax == 1 ? c[1] : c[2]);
     int ncax = ax == 0 ? nc[0] : (ax == 1 ? nc[1] : nc[2]);
@@ -362,7 +363,8 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
             s.A1 = L.A1;
             s.A2 = L.A2;
             s.e = L.e;
-            const float us = fine_start(s, d2, L.u, L.Pa - d2 * L.D2a, ue, Pb - d2 * D2b);
+            // explicit multiply-adds: both engines round the start alike
+            const float us = fine_start(s, d2, L.u, fmaf(-d2, L.D2a, L.Pa), ue, fmaf(-d2, D2b, Pb));
             const float Ds = fmaf(-L.e, us, 1.0f);
             L.Pa = fmaf(fmaf(L.A2, us, L.A1), us, L.A0);
             L.D2a = Ds * Ds;

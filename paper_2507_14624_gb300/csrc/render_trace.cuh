@@ -169,7 +169,7 @@ struct Stats {
 // 1/256 of the skipped length to cover rounding.
 __device__ __forceinline__ float fine_start(const Seg& s, float d2, float u0, float f0, float u1, float f1) {
     if (!(f0 < 0.0f) || !(f1 >= 0.0f) || !(u1 > u0)) return u0;
-    const float a = s.A2 - d2 * s.e * s.e;
+    const float a = fmaf(-__fmul_rn(d2, s.e), s.e, s.A2);
     float us;
     if (a >= 0.0f) {
         us = fmaf(u1 - u0, __fdividef(-f0, f1 - f0), u0);
@@ -280,7 +280,8 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
                     return true;
                 }
             }
-            const float us = fine_start(s, d2, u, Pa - d2 * D2a, ue, Pb - d2 * D2b);
+            // explicit multiply-adds: both engines round the start alike
+            const float us = fine_start(s, d2, u, fmaf(-d2, D2a, Pa), ue, fmaf(-d2, D2b, Pb));
             const float Ds = fmaf(-s.e, us, 1.0f);
             if (fine_walk<NRMF, COUNT>(g, s, pbase, us, ue, fmaf(fmaf(s.A2, us, s.A1), us, s.A0), Ds * Ds, I * k, J * k,
                                        I * k + k - 1, J * k + k - 1, out, st, step_limited))
@@ -526,12 +527,16 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
             tm[a] = step[a] == 0 ? kInf
                                  : (grid_plane(og[a], g.spacing, c[a] + (step[a] > 0 ? 1 : 0)) - Xa[a]) *
                                        frcp(Wa[a]);
-        int ax = 0;
-        if (tm[1] < tm[ax]) ax = 1;
-        if (tm[2] < tm[ax]) ax = 2;
-        int nxt = c[ax] + step[ax];
-        bool last_cell = step[ax] == 0 || nxt < 0 || nxt > nc[ax] - 1;
-        float t_out = last_cell ? kInf : tm[ax];
+        // first exit, ties to the lower axis; selects rather than run-time
+        // indices keep the per-axis arrays in registers (no stack frame)
+        int ax = tm[1] < tm[0] ? 1 : 0;
+        if (tm[2] < (ax ? tm[1] : tm[0])) ax = 2;
+        const int cax = ax == 0 ? c[0] : (ax == 1 ? c[1] : c[2]);
+        const int sax = ax == 0 ? step[0] : (ax == 1 ? step[1] : step[2]);
+        const int ncax = ax == 0 ? nc[0] : (ax == 1 ? nc[1] : nc[2]);
+        int nxt = cax + sax;
+        bool last_cell = sax == 0 || nxt < 0 || nxt > ncax - 1;
+        float t_out = last_cell ? kInf : (ax == 0 ? tm[0] : (ax == 1 ? tm[1] : tm[2]));
         cells++;
 
         // cage: 8 corner probes, nearest to the entry point first, ties to
@@ -565,7 +570,9 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
         if (n_unknown == 8) saw_unknown = true;
         if (last_cell) break;
         t_in = t_out;
-        c[ax] = nxt;
+        if (ax == 0) c[0] = nxt;
+        else if (ax == 1) c[1] = nxt;
+        else c[2] = nxt;
     }
     res.cls = saw_unknown ? kUnknown : kMiss;
     return res;
