@@ -1,0 +1,87 @@
+"""Host logic of bench.py that needs no GPU: which committed ncu summary a
+launch may use (source hash, register budget), the issue roofline arithmetic
+and the algorithmic-bytes model of the fetch counters."""
+import json
+
+import pytest
+
+import bench
+
+
+def test_occupancy_key_follows_pin_then_autotuner():
+    assert bench.occupancy_key("9", None) == "9"
+    assert bench.occupancy_key("8", {"engine": 1, "occupancy": 2}) == "8"  # a pin wins
+    assert bench.occupancy_key("auto", None) == "8"  # grid default: 8 blocks per SM
+    assert bench.occupancy_key("auto", {"engine": 1, "occupancy": 2}) == "9"
+    assert bench.occupancy_key("auto", {"engine": 1, "occupancy": 1}) == "8"
+    assert bench.occupancy_key("auto", {"engine": 1, "occupancy": 0}) == "8"
+    assert bench.occupancy_key("auto", {"engine": 2, "occupancy": 0}) is None  # loop nest: no count
+
+
+def _profiles(tmp_path, monkeypatch, name, payload):
+    (tmp_path / "profiles").mkdir(exist_ok=True)
+    (tmp_path / "profiles" / f"render_{name}_traffic.json").write_text(json.dumps(payload))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "render_source_sha", lambda workload="room": "abc")
+
+
+def test_summary_is_ignored_when_the_kernel_source_changed(tmp_path, monkeypatch):
+    _profiles(tmp_path, monkeypatch, "room", {"source_sha": "old", "warp_inst_per_launch": 10,
+                                               "dram_bytes_per_launch": 5})
+    assert bench.ncu_summary("room") == {}
+    assert bench.ncu_traffic("room") is None
+    assert bench.issue_roofline("room", 1.0, 2070.0, 152) is None
+
+
+def test_summary_per_register_budget(tmp_path, monkeypatch):
+    _profiles(tmp_path, monkeypatch, "batched", {
+        "source_sha": "abc",
+        "by_occupancy": {"8": {"warp_inst_per_launch": 100, "dram_bytes_per_launch": 7},
+                         "9": {"warp_inst_per_launch": 200, "dram_bytes_per_launch": 9}}})
+    assert bench.ncu_traffic("batched", "8") == 7.0
+    assert bench.ncu_traffic("batched", "9") == 9.0
+    assert bench.ncu_summary("batched") == {}  # a keyed summary needs the budget
+    assert bench.ncu_summary("batched", None) == {}
+
+
+def test_issue_roofline_arithmetic(tmp_path, monkeypatch):
+    # 1258.56 G warp instructions in one second at 2070 MHz on 152 SMs = 100 %
+    _profiles(tmp_path, monkeypatch, "room", {"source_sha": "abc", "warp_inst_per_launch": 1258.56e6,
+                                               "dram_bytes_per_launch": 1})
+    r = bench.issue_roofline("room", 1.0, 2070.0, 152, "8")
+    assert r["peak"] == pytest.approx(1258.6, abs=0.05)
+    assert r["achieved"] == pytest.approx(1258.6, abs=0.05)
+    assert r["frac"] == pytest.approx(1.0, abs=1e-4)
+    assert bench.issue_roofline("room", 2.0, 2070.0, 152, "8")["frac"] == pytest.approx(0.5, abs=1e-4)
+    assert bench.issue_roofline("room", 1.0, None, 152, "8") is None  # no clock sample, no peak
+
+
+def test_bytes_model_counts_each_fetch_kind():
+    c = {"coarse": 1, "fine": 0, "normal": 0, "radiance": 0, "rays": 0}
+    assert bench.bytes_model(c, False, False) == 8  # min + max of a low-resolution texel
+    c = {"coarse": 0, "fine": 1, "normal": 0, "radiance": 0, "rays": 0}
+    assert bench.bytes_model(c, False, False) == 4  # one distance
+    for f16, nb, rb in ((False, 8, 12), (True, 4, 8)):
+        assert bench.bytes_model({"coarse": 0, "fine": 0, "normal": 1, "radiance": 0, "rays": 0}, f16, f16) == nb
+        assert bench.bytes_model({"coarse": 0, "fine": 0, "normal": 0, "radiance": 1, "rays": 0}, f16, f16) == rb
+    # rgb f32 x 3 + class u8 per ray
+    assert bench.bytes_model({"coarse": 0, "fine": 0, "normal": 0, "radiance": 0, "rays": 1}, False, False) == 13
+
+
+def test_committed_summaries_parse():
+    """Every committed traffic summary is JSON with a source hash and the
+    fields the bench reads."""
+    import glob
+    import os
+    files = glob.glob(os.path.join(os.path.dirname(bench.__file__), "profiles", "render_*_traffic.json"))
+    assert files
+    for f in files:
+        d = json.load(open(f))
+        assert "source_sha" in d, f
+        entries = list(d.get("by_occupancy", {}).values())
+        for lv in d.get("levels", {}).values():
+            entries += list(lv["by_occupancy"].values())
+        if not entries:
+            entries = [d]
+        for e in entries:
+            assert ("warp_inst_per_launch" in e) or ("warp_inst_per_ray" in e), f
