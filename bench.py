@@ -344,7 +344,12 @@ def run_lfp(args):
 
     extra = {}
     if not args.no_adjoint and rank == 0:
-        extra["fwd_adj_ms_per_view"] = fwd_adjoint_ms_per_view(torch, lfpk, dev)
+        if len(views) > 1:  # the batched views themselves (FP16 texels, FP32 gradient)
+            extra["fwd_adj_ms_per_view"] = fwd_adjoint_on_views(torch, grid, views, dev)
+            extra["fwd_adj_workload"] = f"{args.workload}: its {len(views)} views, forward with aux + adjoint"
+        else:
+            extra["fwd_adj_ms_per_view"] = fwd_adjoint_ms_per_view(torch, lfpk, dev)
+            extra["fwd_adj_workload"] = "fit: room grid seed 4, 64 views 800x800, forward with aux + adjoint"
     if f16 and rank == 0:
         extra["vs_single_view_fp32"] = single_view_fp32(torch, lfpk, lfp, sc, views, d, n, r, cls, flush,
                                                         value, args.steps)
@@ -437,6 +442,31 @@ def fwd_adjoint_ms_per_view(torch, lfpk, dev, steps=5):
     e1.record()
     torch.cuda.synchronize()
     g.close()
+    return round(e0.elapsed_time(e1) / steps / len(views), 4)
+
+
+def fwd_adjoint_on_views(torch, grid, views, dev, steps=3):
+    """Forward with saved state + adjoint into an FP32 radiance gradient over
+    the given views on the given grid (its launch configuration as tuned);
+    ms per view."""
+    out = grid.render(views, aux=True)
+    grad_rgb = torch.randn_like(out["rgb"])
+    grad = torch.zeros((grid.n_probes, grid.N, grid.N, 3), dtype=torch.float32, device=dev)
+    del out
+    for _ in range(2):
+        out = grid.render(views, aux=True)
+        grid.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
+        del out
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        out = grid.render(views, aux=True)
+        grid.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
+        del out
+    e1.record()
+    torch.cuda.synchronize()
+    del grad, grad_rgb
     return round(e0.elapsed_time(e1) / steps / len(views), 4)
 
 

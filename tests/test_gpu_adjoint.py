@@ -36,6 +36,28 @@ def test_adjoint_matches_fp64_oracle_gradient(reduction):
     assert np.abs(grad.cpu().numpy() - ref).max() <= 1e-4 * scale
 
 
+@pytest.mark.parametrize("reduction", [1, 2, 3])
+def test_adjoint_on_fp16_texels_matches_fp64_oracle_gradient(reduction):
+    """FP16 radiance and normals change which texels a ray reads, not the
+    adjoint: given the forward's saved state, the gradient (always FP32,
+    into the caller's master copy) equals the FP64 oracle's."""
+    import paper_2507_14624_gb300 as lfpk
+    g = synth.Grid(2, 2, 2, 1.0, 32, 8)
+    sc = synth.make_scene(g, 8, 2, [1.0], seed=1)
+    d, n, r = sc.probe_maps()
+    grid = lfpk.ProbeGrid(g, radiance_fmt=lfpk.LFP_TEXEL_F16, normal_fmt=lfpk.LFP_TEXEL_F16)
+    grid.upload(d, n, r)
+    views = [synth.random_view(sc, 101, 48, 48, 60.0), synth.random_view(sc, 77, 33, 65, 70.0)]
+    out = grid.render(views)
+    assert (out["cls"] == 1).float().mean().item() > 0.5
+    gr = torch.randn_like(out["rgb"])
+    grad = grid.render_backward(views, gr, out["cls"], out["probe"], out["uv"], reduction=reduction)
+    ref = oracle.Oracle(g, d, n, r).backward(gr.cpu().double().numpy(), out["cls"].cpu().numpy(),
+                                             out["probe"].cpu().numpy(), out["uv"].cpu().double().numpy())
+    assert grad.dtype == torch.float32
+    assert np.abs(grad.cpu().numpy() - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+
+
 def test_adjoint_matches_central_differences_of_the_gpu_forward():
     """2x2x2 cage, 32x32 maps: rgb is linear in radiance, so the central
     difference of <g, rgb> equals the adjoint up to FP32 rounding (<= 1e-2 rel)."""
