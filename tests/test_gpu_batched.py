@@ -66,3 +66,45 @@ def test_more_than_128_views_span_several_launches():
             for k in ("cls", "texel"):
                 assert torch.equal(batch[k][off:off + v.n_pixels], single[k]), (i, k)
         off += v.n_pixels
+
+
+def test_batched_workload_full_size_sampled_against_oracle():
+    """The batched configuration at full size in the launch form the bench
+    times: 8x8x4 probes at N=512 with FP16 radiance and normals, 32 views of
+    640x480 .. 3840x2160 (87.8 M rays), autotuned, one launch replayed from a
+    CUDA graph. The replay equals a direct render; 500 sampled pixels per view
+    against the FP64 oracle under the FP16 rule of test_gpu_parity
+    (test_fp16_texels_error_against_fp64)."""
+    import numpy as np
+
+    import oracle
+    import paper_2507_14624_gb300 as lfpk
+    from test_gpu_parity import compare
+    sc, views = synth.workload("batched")
+    d, n, r = sc.probe_maps()
+    g = lfpk.ProbeGrid(sc.grid, radiance_fmt=lfpk.LFP_TEXEL_F16, normal_fmt=lfpk.LFP_TEXEL_F16)
+    g.upload(d, n, r)
+    g.autotune(views)
+    graph, gout = g.render_graph(views, aux=False)
+    gout["cls"].fill_(255)
+    graph.replay()
+    direct = g.render(views, aux=True, hit_texel=True)
+    torch.cuda.synchronize()
+    assert torch.equal(gout["cls"], direct["cls"])
+    assert torch.equal(gout["rgb"], direct["rgb"])
+    o = oracle.Oracle(sc.grid, d, n, r)
+    rng = np.random.default_rng(11)
+    off, idx, refs = 0, [], []
+    for v in views:
+        pix = np.sort(rng.choice(v.n_pixels, 500, replace=False))
+        refs.append(o.render(v, pix))
+        idx.append(off + pix)
+        off += v.n_pixels
+    assert off == direct["cls"].numel()
+    sel = torch.tensor(np.concatenate(idx), device="cuda")
+    st = compare({k: t[sel] for k, t in direct.items()},
+                 {k: np.concatenate([x[k] for x in refs]) for k in ("cls", "probe", "texel", "rgb")}, sc.grid.N)
+    print("batched full size, sampled", st)
+    assert st["class_match"] >= 0.999 and st["disagree"] <= 2e-3, st
+    assert st["max_err"] <= 1e-3, st
+    g.close()

@@ -103,3 +103,23 @@ def test_build_refuses_bad_ranges():
     with pytest.raises(lfpk.LfpError) as e:
         g.read_probes()
     assert e.value.status == lfpk.lfp.LFP_ERR_STATE
+
+
+def test_full_size_build_workload_equals_oracle_splat():
+    """The build configuration the bench times: the room grid (64 probes,
+    N=256) from 4 scans of 2^23 directions each (33.5 M points), device-
+    resident cloud, one call for all probes; distances and colours equal to
+    the oracle's splat, normals within the octahedral storage error."""
+    import paper_2507_14624_gb300 as lfpk
+    sc, views = synth.workload("room")
+    pc = synth.scan(sc, synth.scan_positions(sc, 4, 2024), 1 << 23, seed=2025)
+    assert len(pc["xyz"]) > 3e7
+    g = lfpk.ProbeGrid(sc.grid)
+    xyz, rgb = (torch.tensor(pc[k], device="cuda") for k in ("xyz", "rgb"))
+    g.build_from_points(xyz, rgb)
+    d, n, r = _read(g)
+    rd, rn, rr = oracle.splat_probes(pc["xyz"], pc["rgb"], sc.grid.probe_positions(), sc.grid.N)
+    assert np.array_equal(d, rd)
+    assert np.array_equal(r, rr)
+    assert np.abs(n - rn).max() <= 2e-6
+    g.close()
