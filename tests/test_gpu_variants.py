@@ -102,3 +102,34 @@ def test_incoming_direction_normals_match_oracle(name):
     st = compare(out, oracle.Oracle(sc.grid, d, n, r).render(views[0]), sc.grid.N)
     print(name, "incoming", st)
     assert_parity(st)
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_mixed_texel_formats(room, engine):
+    """The four radiance x normal storage combinations on the room frame,
+    both engines. Radiance storage never changes a decision: FP16 radiance
+    with FP32 normals decides every pixel as the all-FP32 grid does, with rgb
+    within FP16 rounding; FP32 radiance with FP16 normals shades every pixel
+    it decides alike exactly as the all-FP32 grid does. Each combination
+    meets the oracle under the FP16 rule."""
+    import paper_2507_14624_gb300 as lfpk
+    sc, views, d, n, r = room
+    F32, F16 = lfpk.LFP_TEXEL_F32, lfpk.LFP_TEXEL_F16
+    outs = {}
+    for rf in (F32, F16):
+        for nf in (F32, F16):
+            g = _grid(sc, d, n, r, radiance_fmt=rf, normal_fmt=nf)
+            outs[rf, nf] = g.render(views, hit_texel=True, engine=engine)
+            g.close()
+    ref = oracle.Oracle(sc.grid, d, n, r).render(views[0])
+    for key, out in outs.items():
+        st = compare(out, ref, sc.grid.N)
+        assert st["class_match"] >= 0.999 and st["disagree"] <= 2e-3 and st["max_err"] <= 1e-3, (key, st)
+    base, rad16 = outs[F32, F32], outs[F16, F32]
+    for k in ("cls", "probe", "texel"):
+        assert torch.equal(base[k], rad16[k]), k
+    assert (base["rgb"] - rad16["rgb"]).abs().max().item() <= 1e-3
+    nrm16 = outs[F32, F16]
+    same = (base["cls"] == nrm16["cls"]) & (base["probe"] == nrm16["probe"]) & (base["texel"] == nrm16["texel"])
+    assert same.float().mean().item() >= 0.999
+    assert torch.equal(base["rgb"][same], nrm16["rgb"][same])
