@@ -133,3 +133,26 @@ def test_mixed_texel_formats(room, engine):
     same = (base["cls"] == nrm16["cls"]) & (base["probe"] == nrm16["probe"]) & (base["texel"] == nrm16["texel"])
     assert same.float().mean().item() >= 0.999
     assert torch.equal(base["rgb"][same], nrm16["rgb"][same])
+
+
+def test_eye_nearest_lookup_adjoint_matches_oracle(tiny):
+    """The texel-fetch eye lookup samples the texel's centre, so the adjoint
+    puts the whole pixel gradient on that one texel: equal to the FP64
+    oracle's gradient, and every nonzero entry is a looked-up texel."""
+    import paper_2507_14624_gb300 as lfpk
+    sc, views, d, n, r = tiny
+    P = sc.grid.probe_positions()
+    v = synth.look_view(P[5], 2.1, -0.3, 70.0, 40, 30)
+    grid = _grid(sc, d, n, r, eye_lookup=lfpk.lfp.LFP_EYE_NEAREST)
+    out = grid.render([v], hit_texel=True)
+    gr = torch.randn_like(out["rgb"])
+    grad = grid.render_backward([v], gr, out["cls"], out["probe"], out["uv"])
+    ref = oracle.Oracle(sc.grid, d, n, r, eye_nearest=True).backward(
+        gr.cpu().double().numpy(), out["cls"].cpu().numpy(), out["probe"].cpu().numpy(),
+        out["uv"].cpu().double().numpy())
+    g = grad.cpu().numpy()
+    assert np.abs(g - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    touched = np.unique(out["texel"].cpu().numpy())
+    nz = np.flatnonzero(np.abs(g[5]).reshape(-1, 3).sum(1))
+    assert set(nz.tolist()) <= set(touched.tolist())
+    assert np.abs(np.delete(g, 5, axis=0)).max() == 0.0
