@@ -6,12 +6,13 @@
 // idle: lanes at different depths of the nest execute one after another, and
 // a warp waits for its slowest ray. Here every loop iteration gives each lane
 // one texel visit at whichever level it is on (the low- and full-resolution
-// visits are the same instructions with different operands); the rare
+// visits are the same instructions with different operands); the
 // transitions (a full-resolution crossing's decision, next segment, probe,
-// cell, ray) run in a side branch, and a
-// lane whose ray is done takes the next ray from its warp's pool of 8x4 ray
-// tiles, refilled from a global queue. Results are identical to the nested
-// engine: the same arithmetic decides every texel.
+// cell, ray) run in a control round that the walk enters once most lanes
+// wait for one, and a lane whose ray is done takes the next ray from its
+// warp's pool of 8x4 ray tiles (8-ray rows near the end of the launch),
+// refilled from a global queue. Results are identical to the nested engine:
+// the same arithmetic decides every texel.
 #include <cuda_runtime.h>
 
 #include "lfp_device.cuh"
@@ -34,6 +35,7 @@ constexpr int kMinBlocks[2] = {8, 9};
 constexpr int kStreamThreads = 128;
 constexpr int kWalkSteps = LFP_STREAM_WALK_STEPS;  // most texel visits per lane between control rounds
 constexpr int kBatchPct = LFP_STREAM_BATCH_PCT;     // transitions run once this % of busy lanes wait
+constexpr int kTailTilesPerWarp = 2;  // tiles per warp handed out as 8-ray rows at the end
 constexpr unsigned kFull = 0xffffffffu;
 
 enum Mode : int {
@@ -545,7 +547,12 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
     unsigned long long acc[kNumCounters];
     if (COUNT)
         for (int q = 0; q < kNumCounters; ++q) acc[q] = 0;
-    int pool_tile = 0, pool_next = 32;  // warp-uniform ray pool: one 8x4 tile
+    // warp-uniform ray pool: slots [next, end) of tile pool_tile, packed in
+    // `pool` (next in bits 0-5, end in bits 6-11: one register). The queue
+    // hands out whole 8x4 tiles, and the last kTailTilesPerWarp tiles per
+    // warp of the grid as 8-ray rows, so near the end of the launch no warp
+    // holds many unstarted rays while others have run dry.
+    int pool_tile = 0, pool = 0;
     bool exhausted = false;
     for (;;) {
         // ---- control round: every transition runs once, in pipeline order,
@@ -570,18 +577,26 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
         // refill idle lanes from the warp's pool (warp-synchronous)
         unsigned idle = __ballot_sync(kFull, L.mode == kIdle);
         while (idle != 0u && !exhausted) {
-            if (pool_next >= 32) {
+            if ((pool & 63) >= (pool >> 6)) {
                 int t = 0;
                 if (lane == 0) t = (int)atomicAdd(queue, 1u);
                 t = __shfl_sync(kFull, t, 0);
-                if (t >= vb.total_tiles) {
-                    exhausted = true;
-                    break;
+                const int t_split = max(vb.total_tiles - kTailTilesPerWarp * (int)gridDim.x * (kStreamThreads / 32), 0);
+                if (t < t_split) {
+                    pool_tile = t;
+                    pool = 32 << 6;
+                } else {
+                    const int sub = t - t_split;
+                    pool_tile = t_split + (sub >> 2);
+                    if (pool_tile >= vb.total_tiles) {
+                        exhausted = true;
+                        break;
+                    }
+                    pool = ((sub & 3) * 8) | (((sub & 3) * 8 + 8) << 6);
                 }
-                pool_tile = t;
-                pool_next = 0;
             }
-            int avail = 32 - pool_next;
+            const int pool_next = pool & 63;
+            int avail = (pool >> 6) - pool_next;
             int rank = __popc(idle & lanes_below);
             if (L.mode == kIdle && rank < avail) {
                 st = Stats<COUNT>();
@@ -589,7 +604,7 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
                 probes = 0;
                 start_ray<NEAREST>(g, vb, pool_tile, pool_next + rank, L);  // kRayDone rays are written next round
             }
-            pool_next += min(__popc(idle), avail);
+            pool += min(__popc(idle), avail);
             idle = __ballot_sync(kFull, L.mode == kIdle);
         }
         if (exhausted && L.mode == kIdle) L.mode = kExit;
