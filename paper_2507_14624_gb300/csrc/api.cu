@@ -193,8 +193,15 @@ bool valid_tile(int w, int h) {
            (w == 32 && h == 8);
 }
 
+// queue: a work-queue head of the caller's (the frame loop's, whose launches
+// overlap one another), else the grid's own.
 lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const OutDev& out,
                        const lfp_render_opts* opts, cudaStream_t s, unsigned* queue = nullptr) {
+    // A launch alone on the GPU ends with a tail where warps run dry while
+    // others still hold rays; the streaming engine hands its last two tiles
+    // per warp out as half tiles to even it out. Overlapping launches fill
+    // each other's tails, so there the split would only add queue traffic.
+    const bool overlapped = queue != nullptr;
     if (!queue) queue = g->tile_counter;  // the persistent launches' work-queue head
     int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0, engine = g->engine, occ = g->stream_occ;
     if (opts) {
@@ -236,6 +243,7 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
             }
             vb.total_tiles = (int)tiles;
             int blocks = (int)std::min<long long>(g->stream_blocks[occ], (tiles + 3) / 4);
+            vb.tail_tiles = overlapped ? 0 : 2 * blocks * (kStreamThreadsPerBlock / 32);
             LFP_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
             LFP_CUDA(launch_render_stream(gd, g->desc.radiance_fmt, g->desc.normal_fmt, vb, out, queue,
                                           blocks, occ, s));

@@ -53,6 +53,7 @@ struct ViewDev {
 struct ViewBatch {
     int n;
     int total_tiles;
+    int tail_tiles;  // streaming engine: the last tail_tiles tiles go out as 16-ray halves
     int tile_w, tile_h;
     ViewDev v[kMaxViewsPerLaunch];
 };

@@ -8,6 +8,7 @@
 namespace lfp {
 
 constexpr int kMaxSplatProbes = 2048;
+constexpr int kStreamThreadsPerBlock = 128;  // streaming engine: 4 warps per block
 
 struct RenderLaunch {
     int flat;                 // full-resolution march only (Appendix A RayMarching)

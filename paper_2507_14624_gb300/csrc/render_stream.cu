@@ -10,7 +10,7 @@
 // transitions (a full-resolution crossing's decision, next segment, probe,
 // cell, ray) run in a control round that the walk enters once most lanes
 // wait for one, and a lane whose ray is done takes the next ray from its
-// warp's pool of 8x4 ray tiles (8-ray rows near the end of the launch),
+// warp's pool of 8x4 ray tiles (16-ray halves near the end of the launch),
 // refilled from a global queue. Results are identical to the nested engine:
 // the same arithmetic decides every texel.
 #include <cuda_runtime.h>
@@ -32,10 +32,9 @@ using namespace trace;
 #endif
 // resident blocks per SM of the two register budgets (64 and 56 registers)
 constexpr int kMinBlocks[2] = {8, 9};
-constexpr int kStreamThreads = 128;
+constexpr int kStreamThreads = kStreamThreadsPerBlock;
 constexpr int kWalkSteps = LFP_STREAM_WALK_STEPS;  // most texel visits per lane between control rounds
 constexpr int kBatchPct = LFP_STREAM_BATCH_PCT;     // transitions run once this % of busy lanes wait
-constexpr int kTailTilesPerWarp = 2;  // tiles per warp handed out as 8-ray rows at the end
 constexpr unsigned kFull = 0xffffffffu;
 
 enum Mode : int {
@@ -549,9 +548,9 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
         for (int q = 0; q < kNumCounters; ++q) acc[q] = 0;
     // warp-uniform ray pool: slots [next, end) of tile pool_tile, packed in
     // `pool` (next in bits 0-5, end in bits 6-11: one register). The queue
-    // hands out whole 8x4 tiles, and the last kTailTilesPerWarp tiles per
-    // warp of the grid as 8-ray rows, so near the end of the launch no warp
-    // holds many unstarted rays while others have run dry.
+    // hands out whole 8x4 tiles, and the last vb.tail_tiles tiles as 16-ray
+    // halves, so near the end of the launch no warp holds many unstarted
+    // rays while others have run dry.
     int pool_tile = 0, pool = 0;
     bool exhausted = false;
     for (;;) {
@@ -581,18 +580,18 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
                 int t = 0;
                 if (lane == 0) t = (int)atomicAdd(queue, 1u);
                 t = __shfl_sync(kFull, t, 0);
-                const int t_split = max(vb.total_tiles - kTailTilesPerWarp * (int)gridDim.x * (kStreamThreads / 32), 0);
+                const int t_split = max(vb.total_tiles - vb.tail_tiles, 0);
                 if (t < t_split) {
                     pool_tile = t;
                     pool = 32 << 6;
                 } else {
                     const int sub = t - t_split;
-                    pool_tile = t_split + (sub >> 2);
+                    pool_tile = t_split + (sub >> 1);
                     if (pool_tile >= vb.total_tiles) {
                         exhausted = true;
                         break;
                     }
-                    pool = ((sub & 3) * 8) | (((sub & 3) * 8 + 8) << 6);
+                    pool = ((sub & 1) * 16) | (((sub & 1) * 16 + 16) << 6);
                 }
             }
             const int pool_next = pool & 63;
