@@ -187,7 +187,9 @@ lfp_status lfp_upload_probes(lfp_grid* grid, int first_probe, int count,
  * `views` is host memory, read before the call returns. rgb [P][3] f32 and
  * cls [P] u8 are required; aux_probe [P] i32 and aux_uv [P][2] f32 are the
  * saved state for lfp_render_backward and may be NULL. Pixels that are not
- * HIT get rgb 0. Returns LFP_ERR_STATE if any probe was never uploaded. */
+ * HIT get rgb 0. Returns LFP_ERR_STATE if any probe was never uploaded, and
+ * LFP_ERR_INVALID_ARG if a view has more than 2^31 pixels or a group of 128
+ * consecutive views more than 2^30 ray tiles of 8 x 4 pixels. */
 lfp_status lfp_render(lfp_grid* grid, const lfp_view* views, int n_views,
                       float* rgb, uint8_t* cls, int32_t* aux_probe, float* aux_uv,
                       void* cuda_stream);

@@ -239,7 +239,7 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
                 const lfp_view& v = views[first + i];
                 vb.v[i] = view_dev(v, 8, 4, (int)tiles);
                 tiles += (long long)vb.v[i].tiles_x * ((v.H + 3) / 4);
-                if (tiles > (1LL << 31) - 1) return LFP_ERR_INVALID_ARG;
+                if (tiles > kMaxTilesPerLaunch) return LFP_ERR_INVALID_ARG;
             }
             vb.total_tiles = (int)tiles;
             int blocks = (int)std::min<long long>(g->stream_blocks[occ], (tiles + 3) / 4);
@@ -269,7 +269,7 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
             const lfp_view& v = views[first + i];
             vb.v[i] = view_dev(v, tw, th, (int)tiles);
             tiles += (long long)vb.v[i].tiles_x * ((v.H + th - 1) / th);
-            if (tiles > (1LL << 31) - 1) return LFP_ERR_INVALID_ARG;
+            if (tiles > kMaxTilesPerLaunch) return LFP_ERR_INVALID_ARG;
         }
         vb.total_tiles = (int)tiles;
         if (L.persistent) LFP_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));

@@ -9,6 +9,10 @@ namespace lfp {
 
 constexpr int kMaxSplatProbes = 2048;
 constexpr int kStreamThreadsPerBlock = 128;  // streaming engine: 4 warps per block
+// Ray tiles per launch. The persistent kernels' work-queue head (an unsigned
+// counter read as int) runs past the last tile by one grab per warp, plus
+// the tail's half tiles: a bound far below the int range keeps it positive.
+constexpr long long kMaxTilesPerLaunch = 1LL << 30;
 
 struct RenderLaunch {
     int flat;                 // full-resolution march only (Appendix A RayMarching)

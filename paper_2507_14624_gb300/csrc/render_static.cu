@@ -170,7 +170,7 @@ extern "C" lfp_status lfp_render_static(lfp_grid* grid, const lfp_view* views, i
     long long tiles = 0;
     for (int i = 0; i < n_views; ++i) {
         tiles += (long long)((views[i].W + kTileW - 1) / kTileW) * ((views[i].H + kTileH - 1) / kTileH);
-        if (tiles > (1LL << 31) - 1) return LFP_ERR_CAPACITY;
+        if (tiles > kMaxTilesPerLaunch) return LFP_ERR_CAPACITY;
     }
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return LFP_ERR_CUDA;
