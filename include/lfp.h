@@ -48,6 +48,7 @@ typedef enum {
     LFP_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
     LFP_ERR_STATE = 4,       /* call order violated (e.g. render before upload) */
     LFP_ERR_CAPACITY = 5,    /* request larger than a fixed-size buffer allows */
+    LFP_ERR_BOUNDS = 6,      /* an index out of range was caught (lfp_check_flags) */
     LFP_WARN_STEPLIMIT = 100 /* some ray hit the per-ray step cap (class 3) */
 } lfp_status;
 
@@ -262,7 +263,11 @@ lfp_status lfp_render_backward_ex(lfp_grid* grid, const lfp_view* views, int n_v
 lfp_status lfp_set_radiance(lfp_grid* grid, const float* dev_radiance_f32, void* cuda_stream);
 
 /* Synchronise the stream and report (then clear) the device flag word:
- * LFP_WARN_STEPLIMIT if some ray reached max_steps since the last call. */
+ * LFP_ERR_BOUNDS if an index out of range was caught since the last call (an
+ * adjoint given saved state whose probe index is outside the grid, or, in
+ * the checked library liblfp_checked.so, any texel index of a render or
+ * adjoint; the access was redirected to texel 0), else LFP_WARN_STEPLIMIT if
+ * some ray reached max_steps, else LFP_OK. */
 lfp_status lfp_check_flags(lfp_grid* grid, void* cuda_stream);
 
 /* Device bytes the grid's probe storage takes for a descriptor (maps + mip),

@@ -1,7 +1,10 @@
 """Compile the CUDA library liblfp.so for sm_103a (in-tree, git-ignored).
 
 The translation units are compiled in parallel with nvcc and linked into a
-shared library exporting the C ABI of include/lfp.h.
+shared library exporting the C ABI of include/lfp.h. build(checked=True)
+makes liblfp_checked.so from the same sources with -DLFP_BOUNDS_CHECK: every
+texel index of a render or adjoint is tested (see lfp_check_flags); the
+binding loads it when LFP_CHECKED=1.
 """
 import os
 import subprocess
@@ -12,6 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblfp.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "liblfp_checked.so")
 SOURCES = ["render.cu", "render_stream.cu", "render_static.cu", "support.cu", "api.cu", "levels.cu",
            "build_probes.cu"]
 HEADERS = ["lfp_device.cuh", "lfp_internal.h", "render_trace.cuh"]
@@ -31,17 +36,19 @@ def _newest_input():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib, out_dir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *(["-DLFP_BOUNDS_CHECK"] if checked else []), "-c", os.path.join(CSRC, src),
+               "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
@@ -54,12 +61,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

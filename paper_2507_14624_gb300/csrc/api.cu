@@ -360,6 +360,7 @@ const char* lfp_status_string(lfp_status s) {
         case LFP_ERR_CUDA: return "CUDA error";
         case LFP_ERR_STATE: return "invalid call order (e.g. probes not uploaded)";
         case LFP_ERR_CAPACITY: return "request exceeds a fixed-size buffer (e.g. more than LFP_STATIC_MAX_VIEWS views)";
+        case LFP_ERR_BOUNDS: return "an index out of range was caught (redirected to texel 0)";
         case LFP_WARN_STEPLIMIT: return "some rays reached the step limit";
     }
     return "unknown status";
@@ -757,8 +758,8 @@ lfp_status lfp_render_backward_ex(lfp_grid* g, const lfp_view* views, int n_view
             pb.out_offset[i] = v.out_offset;
             pb.begin[i + 1] = pb.begin[i] + (long long)v.W * v.H;
         }
-        LFP_CUDA(launch_backward(g->desc.N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_radiance, reduction,
-                                 (cudaStream_t)stream));
+        LFP_CUDA(launch_backward(g->desc.N, (int)g->P, g->flags, pb, grad_rgb, cls, aux_probe, aux_uv, grad_radiance,
+                                 reduction, (cudaStream_t)stream));
     }
     return LFP_OK;
 }
@@ -781,6 +782,7 @@ lfp_status lfp_check_flags(lfp_grid* g, void* stream) {
     LFP_CUDA(cudaMemcpyAsync(&flags, g->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     LFP_CUDA(cudaStreamSynchronize(s));
     LFP_CUDA(cudaMemsetAsync(g->flags, 0, sizeof(unsigned), s));
+    if (flags & kFlagBounds) return LFP_ERR_BOUNDS;
     return (flags & 1u) ? LFP_WARN_STEPLIMIT : LFP_OK;
 }
 

@@ -37,8 +37,29 @@ struct GridDev {
     const float2* mip;
     const void* nrm;
     const void* rad;
-    unsigned* flags;          // bit 0: step limit reached
+    unsigned* flags;          // bit 0: step limit reached; bit 1: texel index out of range (checked builds)
 };
+
+// Checked builds (-DLFP_BOUNDS_CHECK, liblfp_checked.so) test every texel
+// index of the probe maps and of the gradient before the access: an index
+// out of range sets kFlagBounds in the grid's flag word and is replaced by
+// texel (0, 0), so the access stays inside the map. Release builds compile
+// the test away.
+constexpr unsigned kFlagBounds = 2u;
+#ifdef LFP_BOUNDS_CHECK
+#define LFP_CHECK_TEXEL(flags, in_range, i, j)   \
+    do {                                          \
+        if (!(in_range)) {                        \
+            atomicOr((flags), lfp::kFlagBounds);  \
+            (i) = 0;                              \
+            (j) = 0;                              \
+        }                                         \
+    } while (0)
+#else
+#define LFP_CHECK_TEXEL(flags, in_range, i, j) \
+    do {                                        \
+    } while (0)
+#endif
 
 struct ViewDev {
     float px, py, pz;

@@ -37,10 +37,12 @@ cudaError_t launch_convert_radiance(const float* rgb, void* rad, int rad_fmt, lo
 // per-block min/max of the distance maps for `count` probes
 cudaError_t launch_build_mip(const float* dist, float2* mip, int count, int N, int M, cudaStream_t s);
 // adjoint scatter into grad_radiance [P][N][N][3]; reduction: 1 per-pixel
-// atomics, 2 warp-aggregated atomics, 3 block-local sort by texel
-cudaError_t launch_backward(int N, const PixBatch& pb, const float* grad_rgb, const uint8_t* cls,
-                            const int32_t* aux_probe, const float* aux_uv, float* grad_rad, int reduction,
-                            cudaStream_t s);
+// atomics, 2 warp-aggregated atomics, 3 block-local sort by texel. HIT
+// pixels whose saved probe index is outside [0, P) are skipped and set
+// kFlagBounds in *flags.
+cudaError_t launch_backward(int N, int P, unsigned* flags, const PixBatch& pb, const float* grad_rgb,
+                            const uint8_t* cls, const int32_t* aux_probe, const float* aux_uv, float* grad_rad,
+                            int reduction, cudaStream_t s);
 
 // probe maps from a point cloud (build_probes.cu): at most kMaxSplatProbes
 // probes per splat launch (their positions sit in shared memory); keys [count][N][N] set to

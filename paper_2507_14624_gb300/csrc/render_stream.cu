@@ -237,6 +237,12 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     L.A2 = s.A2;
     L.dir0 = s.dir[0];
     L.dir1 = s.dir[1];
+    {
+        int p = L.probe, unused = 0;
+        LFP_CHECK_TEXEL(g.flags, (unsigned)p < (unsigned)(g.nx * g.ny * g.nz), p, unused);
+        L.probe = p;
+        (void)unused;
+    }
     L.dmap = g.dist + (size_t)L.probe * g.N * g.N;
     L.mmap = g.mip + (size_t)L.probe * g.M * g.M;
     const int k = g.k, N = g.N;
@@ -315,10 +321,14 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
     float D2b = Db * Db;
     float v, vmax = 0.0f;
     if (L.level) {
-        v = __ldg(L.dmap + (L.j * N + L.i));
+        int i = L.i, j = L.j;
+        LFP_CHECK_TEXEL(g.flags, (unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N, i, j);
+        v = __ldg(L.dmap + (j * N + i));
         if (COUNT) st.fine++;
     } else {
-        float2 mm = __ldg(L.mmap + (L.j * M + L.i));
+        int i = L.i, j = L.j;
+        LFP_CHECK_TEXEL(g.flags, (unsigned)i < (unsigned)M && (unsigned)j < (unsigned)M, i, j);
+        float2 mm = __ldg(L.mmap + (j * M + i));
         v = mm.x;
         vmax = mm.y;
         if (COUNT) st.coarse++;
@@ -394,7 +404,9 @@ __device__ __forceinline__ void decide(const GridDev& g, Lane& L, Stats<COUNT>& 
     float d = v, dk = d * g.kappa;
     L.mode = kUnknownRes;
     if (g.two_way || lane_r2(fminf(fmaxf(CF(kTstar), ta), tb)) <= dk * dk) {
-        float2 no = NrmTexel<NRMF>::load(g.nrm, (size_t)L.probe * N * N + (size_t)L.j * N + L.i);
+        int i = L.i, j = L.j;
+        LFP_CHECK_TEXEL(g.flags, (unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N, i, j);
+        float2 no = NrmTexel<NRMF>::load(g.nrm, (size_t)L.probe * N * N + (size_t)j * N + i);
         float3 n = oct_decode_unnorm(no.x, no.y);
         const float3 w = ray_w();
         if (COUNT) st.normal++;

@@ -200,7 +200,9 @@ __device__ bool fine_walk(const GridDev& g, const Seg& s, size_t pbase, float u0
         float Pb = fmaf(fmaf(s.A2, ue, s.A1), ue, s.A0);
         float Db = fmaf(-s.e, ue, 1.0f);
         float D2b = Db * Db;
-        float d = __ldg(g.dist + pbase + (size_t)j * N + i);
+        int ic = i, jc = j;
+        LFP_CHECK_TEXEL(g.flags, (unsigned)ic < (unsigned)N && (unsigned)jc < (unsigned)N, ic, jc);
+        float d = __ldg(g.dist + pbase + (size_t)jc * N + ic);
         float d2 = d * d;
         if (COUNT) st.fine++;
         st.steps++;
@@ -210,7 +212,7 @@ __device__ bool fine_walk(const GridDev& g, const Seg& s, size_t pbase, float u0
             float dk = d * g.kappa;
             out.cls = kUnknown;  // unless the normal test passes below
             if (g.two_way || r2_tau(s, fminf(fmaxf(s.tstar, ta), tb)) <= dk * dk) {
-                float2 no = NrmTexel<NRMF>::load(g.nrm, pbase + (size_t)j * N + i);
+                float2 no = NrmTexel<NRMF>::load(g.nrm, pbase + (size_t)jc * N + ic);
                 float3 n = oct_decode_unnorm(no.x, no.y);
                 if (COUNT) st.normal++;
                 if ((n.x * s.w.x + n.y * s.w.y + n.z * s.w.z) < 0.0f) {
@@ -246,6 +248,11 @@ template <int NRMF, bool COUNT, bool FLAT>
 __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decision& out, Stats<COUNT>& st,
                               bool& step_limited) {
     const int N = g.N, M = g.M, k = g.k;
+    {
+        int unused = 0;
+        LFP_CHECK_TEXEL(g.flags, (unsigned)probe < (unsigned)(g.nx * g.ny * g.nz), probe, unused);
+        (void)unused;
+    }
     size_t pbase = (size_t)probe * N * N;
     if (FLAT)  // Appendix A RayMarching: the full-resolution map only
         return fine_walk<NRMF, COUNT>(g, s, pbase, 0.0f, s.u_end, s.A0, 1.0f, s.lo[0], s.lo[1], s.hi[0], s.hi[1],
@@ -266,7 +273,9 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
         float Pb = fmaf(fmaf(s.A2, ue, s.A1), ue, s.A0);
         float Db = fmaf(-s.e, ue, 1.0f);
         float D2b = Db * Db;
-        float2 mm = __ldg(mip + (size_t)J * M + I);
+        int Ic = I, Jc = J;
+        LFP_CHECK_TEXEL(g.flags, (unsigned)Ic < (unsigned)M && (unsigned)Jc < (unsigned)M, Ic, Jc);
+        float2 mm = __ldg(mip + (size_t)Jc * M + Ic);
         float d2 = mm.x * mm.x;
         if (COUNT) st.coarse++;
         st.steps++;
@@ -390,11 +399,15 @@ __device__ __forceinline__ float3 shade(const GridDev& g, int probe, float u, fl
     int idx[4];
     float w[4];
     bilinear_taps(g.N, u, v, idx, w);
-    size_t base = (size_t)probe * g.N * g.N;
+    int pc = probe, zero = 0;
+    LFP_CHECK_TEXEL(g.flags, (unsigned)pc < (unsigned)(g.nx * g.ny * g.nz), pc, zero);
+    size_t base = (size_t)pc * g.N * g.N;
     float3 c = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        float3 t = RadTexel<RADF>::load(g.rad, base + idx[q]);
+        int tq = idx[q];
+        LFP_CHECK_TEXEL(g.flags, (unsigned)tq < (unsigned)(g.N * g.N), tq, zero);
+        float3 t = RadTexel<RADF>::load(g.rad, base + tq);
         c.x = fmaf(w[q], t.x, c.x);
         c.y = fmaf(w[q], t.y, c.y);
         c.z = fmaf(w[q], t.z, c.z);

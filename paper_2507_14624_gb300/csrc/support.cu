@@ -65,7 +65,7 @@ __global__ void build_mip_kernel(const float* __restrict__ dist, float2* __restr
 }
 
 // Adjoint: for every HIT pixel add w_k * g_c into the 4 bilinear taps.
-__global__ void backward_kernel(int N, PixBatch pb, const float* __restrict__ grad_rgb,
+__global__ void backward_kernel(int N, int P, unsigned* flags, PixBatch pb, const float* __restrict__ grad_rgb,
                                 const uint8_t* __restrict__ cls, const int32_t* __restrict__ aux_probe,
                                 const float* __restrict__ aux_uv, float* __restrict__ grad_rad) {
     long long total = pb.begin[pb.n];
@@ -79,10 +79,18 @@ __global__ void backward_kernel(int N, PixBatch pb, const float* __restrict__ gr
         long long o = pb.out_offset[lo] + (q - pb.begin[lo]);
         if (cls[o] != kHit) continue;
         int p = aux_probe[o];
-        if (p < 0) continue;
+        if ((unsigned)p >= (unsigned)P) {  // not the saved state of a render of this grid
+            atomicOr(flags, kFlagBounds);
+            continue;
+        }
         int idx[4];
         float w[4];
         bilinear_taps(N, aux_uv[2 * o], aux_uv[2 * o + 1], idx, w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int zero = 0;
+            LFP_CHECK_TEXEL(flags, (unsigned)idx[k] < (unsigned)(N * N), idx[k], zero);
+        }
         float g0 = grad_rgb[3 * o], g1 = grad_rgb[3 * o + 1], g2 = grad_rgb[3 * o + 2];
         float* base = grad_rad + (size_t)p * N * N * 3;
 #pragma unroll
@@ -101,7 +109,7 @@ __global__ void backward_kernel(int N, PixBatch pb, const float* __restrict__ gr
 // pixels of a row, so equal texels come in runs of neighbouring lanes: a
 // segmented sum over the runs (five shuffle steps) leaves each run's total
 // in its last lane, which does the atomics.
-__global__ void backward_warp_kernel(int N, PixBatch pb, const float* __restrict__ grad_rgb,
+__global__ void backward_warp_kernel(int N, int P, unsigned* flags, PixBatch pb, const float* __restrict__ grad_rgb,
                                      const uint8_t* __restrict__ cls, const int32_t* __restrict__ aux_probe,
                                      const float* __restrict__ aux_uv, float* __restrict__ grad_rad) {
     const unsigned full = 0xffffffffu;
@@ -123,13 +131,22 @@ __global__ void backward_warp_kernel(int N, PixBatch pb, const float* __restrict
             }
             o = pb.out_offset[lo] + (q - pb.begin[lo]);
             p = aux_probe[o];
-            hit = cls[o] == kHit && p >= 0;
+            hit = cls[o] == kHit;
+            if (hit && (unsigned)p >= (unsigned)P) {  // not the saved state of a render of this grid
+                atomicOr(flags, kFlagBounds);
+                hit = false;
+            }
         }
         int idx[4];
         float w[4] = {0.f, 0.f, 0.f, 0.f};
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         if (hit) {
             bilinear_taps(N, aux_uv[2 * o], aux_uv[2 * o + 1], idx, w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                int zero = 0;
+                LFP_CHECK_TEXEL(flags, (unsigned)idx[k] < (unsigned)(N * N), idx[k], zero);
+            }
             g0 = grad_rgb[3 * o];
             g1 = grad_rgb[3 * o + 1];
             g2 = grad_rgb[3 * o + 2];
@@ -170,7 +187,7 @@ __global__ void backward_warp_kernel(int N, PixBatch pb, const float* __restrict
 constexpr int kSortThreads = 256;
 constexpr int kSortTaps = 4 * kSortThreads;
 
-__global__ void __launch_bounds__(kSortThreads) backward_sort_kernel(int N, PixBatch pb,
+__global__ void __launch_bounds__(kSortThreads) backward_sort_kernel(int N, int P, unsigned* flags, PixBatch pb,
                                                                      const float* __restrict__ grad_rgb,
                                                                      const uint8_t* __restrict__ cls,
                                                                      const int32_t* __restrict__ aux_probe,
@@ -194,13 +211,22 @@ __global__ void __launch_bounds__(kSortThreads) backward_sort_kernel(int N, PixB
             }
             o = pb.out_offset[lo] + (q - pb.begin[lo]);
             p = aux_probe[o];
-            hit = cls[o] == kHit && p >= 0;
+            hit = cls[o] == kHit;
+            if (hit && (unsigned)p >= (unsigned)P) {  // not the saved state of a render of this grid
+                atomicOr(flags, kFlagBounds);
+                hit = false;
+            }
         }
         int idx[4];
         float w[4] = {0.f, 0.f, 0.f, 0.f};
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         if (hit) {
             bilinear_taps(N, aux_uv[2 * o], aux_uv[2 * o + 1], idx, w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                int zero = 0;
+                LFP_CHECK_TEXEL(flags, (unsigned)idx[k] < (unsigned)(N * N), idx[k], zero);
+            }
             g0 = grad_rgb[3 * o];
             g1 = grad_rgb[3 * o + 1];
             g2 = grad_rgb[3 * o + 2];
@@ -274,18 +300,18 @@ cudaError_t launch_build_mip(const float* dist, float2* mip, int count, int N, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_backward(int N, const PixBatch& pb, const float* grad_rgb, const uint8_t* cls,
-                            const int32_t* aux_probe, const float* aux_uv, float* grad_rad, int reduction,
-                            cudaStream_t s) {
+cudaError_t launch_backward(int N, int P, unsigned* flags, const PixBatch& pb, const float* grad_rgb,
+                            const uint8_t* cls, const int32_t* aux_probe, const float* aux_uv, float* grad_rad,
+                            int reduction, cudaStream_t s) {
     long long total = pb.begin[pb.n];
     if (total == 0) return cudaSuccess;
     if (reduction == 2)
-        backward_warp_kernel<<<blocks_for(total), kThreads, 0, s>>>(N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
+        backward_warp_kernel<<<blocks_for(total), kThreads, 0, s>>>(N, P, flags, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
     else if (reduction == 3)
         backward_sort_kernel<<<(int)std::min<long long>((total + kSortThreads - 1) / kSortThreads, 1 << 20),
-                               kSortThreads, 0, s>>>(N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
+                               kSortThreads, 0, s>>>(N, P, flags, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
     else
-        backward_kernel<<<blocks_for(total), kThreads, 0, s>>>(N, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
+        backward_kernel<<<blocks_for(total), kThreads, 0, s>>>(N, P, flags, pb, grad_rgb, cls, aux_probe, aux_uv, grad_rad);
     return cudaGetLastError();
 }
 

@@ -2,8 +2,9 @@
 
 Every function here has the name of the C entry point it calls; every step of
 the tracer runs in the CUDA library. PyTorch supplies device memory (tensor
-data pointers) and streams. The library is loaded from the package directory;
-if it is missing the import fails -- there is no fallback.
+data pointers) and streams. The library is loaded from the package directory
+(liblfp.so, or with LFP_CHECKED=1 the checked build liblfp_checked.so); if it
+is missing the import fails -- there is no fallback.
 """
 from __future__ import annotations
 
@@ -11,10 +12,11 @@ import ctypes
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "liblfp.so")
+LIB_PATH = os.path.join(PKG, "liblfp_checked.so" if os.environ.get("LFP_CHECKED") == "1" else "liblfp.so")
 
 # status codes
 LFP_OK, LFP_ERR_INVALID_ARG, LFP_ERR_OOM, LFP_ERR_CUDA, LFP_ERR_STATE, LFP_ERR_CAPACITY = 0, 1, 2, 3, 4, 5
+LFP_ERR_BOUNDS = 6
 LFP_STATIC_MAX_VIEWS = 4096
 LFP_WARN_STEPLIMIT = 100
 LFP_TEXEL_F32, LFP_TEXEL_F16 = 0, 1

@@ -96,7 +96,7 @@ def test_null_arguments_are_rejected(lib):
 
 
 def test_status_strings(lib):
-    for s in (0, 1, 2, 3, 4, 100):
+    for s in (0, 1, 2, 3, 4, 5, 6, 100):
         assert len(lib.lfp_status_string(s)) >= 2
     assert lib.lfp_status_string(999) == "unknown status"
 
