@@ -116,3 +116,23 @@ def test_fit_reaches_the_noise_floor():
     rad, hist = fit.fit_radiance(grid, views, targets, steps=300, lr=2e-2, seed=404)
     mse = hist[-1][1]
     assert 0.5 * sigma ** 2 <= mse <= 2.0 * sigma ** 2, hist[-1]
+
+
+def test_fit_checkpoint_and_resume(tmp_path):
+    """A fit stopped after 6 of 12 steps and resumed from its checkpoint ends
+    where the uninterrupted 12-step fit ends (up to the order of the
+    adjoint's float atomics), with the history of both halves."""
+    from paper_2507_14624_gb300 import fit
+    lfpk, g, sc, v, d, n, r, grid = _setup(N=32, M=8, W=64, H=64)
+    views = [v] + [synth.random_view(sc, 1300 + k, 48, 48, 60.0) for k in range(3)]
+    targets = fit.make_targets(grid, views, sigma=0.01, seed=404)
+    full, hist_full = fit.fit_radiance(grid, views, targets, steps=12, lr=2e-2, seed=7, log_every=1)
+    ck = str(tmp_path / "fit.pt")
+    half, _ = fit.fit_radiance(grid, views, targets, steps=6, lr=2e-2, seed=7, log_every=1, checkpoint=ck)
+    assert torch.load(ck, weights_only=False)["step"] == 5
+    resumed, hist = fit.fit_radiance(grid, views, targets, steps=12, lr=2e-2, seed=99, log_every=1, checkpoint=ck,
+                                     checkpoint_every=4)
+    assert [h[0] for h in hist] == list(range(12))
+    assert torch.load(ck, weights_only=False)["step"] == 11
+    assert (resumed - full).abs().max().item() <= 1e-4
+    assert abs(hist[-1][1] - hist_full[-1][1]) <= 1e-6
