@@ -592,7 +592,9 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
                 int t = 0;
                 if (lane == 0) t = (int)atomicAdd(queue, 1u);
                 t = __shfl_sync(kFull, t, 0);
-                const int t_split = max(vb.total_tiles - vb.tail_tiles, 0);
+                // the 56-register build keeps whole tiles (its register
+                // allocation loses more than the split gains)
+                const int t_split = OCC == 1 ? vb.total_tiles : max(vb.total_tiles - vb.tail_tiles, 0);
                 if (t < t_split) {
                     pool_tile = t;
                     pool = 32 << 6;
