@@ -209,6 +209,13 @@ lfp_status lfp_render_ex(lfp_grid* grid, const lfp_view* views, int n_views,
 lfp_status lfp_autotune(lfp_grid* grid, const lfp_view* views, int n_views,
                         const lfp_outputs* out, lfp_render_opts* best, void* cuda_stream);
 
+/* Make `opts` the grid's default launch configuration, as lfp_autotune does
+ * with the one it picks (e.g. a pick it returned earlier for the same views
+ * and GPU, kept by the caller). Fields left zero keep the current default;
+ * march must be LFP_MARCH_HIER. Host-only, no stream. Errors: INVALID_ARG
+ * (a field out of range or an invalid tile shape). */
+lfp_status lfp_set_defaults(lfp_grid* grid, const lfp_render_opts* opts);
+
 /* Render into HOST memory: one call that runs lfp_render on device buffers
  * owned by the grid and copies rgb [P][3] f32 and cls [P] u8 back, then
  * synchronises the stream. rgb_host / cls_host: host memory (pinned memory

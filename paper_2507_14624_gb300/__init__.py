@@ -42,6 +42,52 @@ def make_views(views) -> tuple:
     return arr, len(views), off
 
 
+_LIB_DIGEST = None
+
+
+def _library_digest() -> str:
+    """sha256 of the loaded CUDA library (a rebuild invalidates tuned picks)."""
+    global _LIB_DIGEST
+    if _LIB_DIGEST is None:
+        import hashlib
+        with open(lfp.LIB_PATH, "rb") as f:
+            _LIB_DIGEST = hashlib.sha256(f.read()).hexdigest()[:16]
+    return _LIB_DIGEST
+
+
+def tune_key(grid, views, device_name: str | None = None) -> str:
+    """Key of an autotuner pick: GPU, library build, grid descriptor and the
+    multiset of view sizes (the views' poses do not enter)."""
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name()
+    d = grid.desc
+    desc = (d.nx, d.ny, d.nz, d.spacing, d.N, d.M, d.radiance_fmt, d.normal_fmt, d.thickness_rel, d.max_steps,
+            d.eye_lookup, d.traversal)
+    sizes = sorted((v.W, v.H) for v in views)
+    return f"{device_name}|{_library_digest()}|{desc}|{sizes}"
+
+
+def _read_tune_cache(path: str) -> dict:
+    import json
+    import os
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)
+
+
+def _write_tune_cache(path: str, key: str, pick: dict) -> None:
+    import json
+    import os
+    data = _read_tune_cache(path)
+    data[key] = {k: (list(v) if isinstance(v, tuple) else v) for k, v in pick.items()}
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class ProbeGrid:
     """A probe grid on the current CUDA device (owns one lfp_grid handle).
 
@@ -182,10 +228,21 @@ class ProbeGrid:
         lfp.lfp_render_ex(self.handle, arr, n, o, opts, _stream_handle(stream))
         return out
 
-    def autotune(self, views, stream=None) -> dict:
+    def autotune(self, views, stream=None, cache: str | None = None) -> dict:
         """Pick the fastest launch configuration for these views (kept as the
-        grid default). Returns it as a dict."""
+        grid default). Returns it as a dict. With `cache` (a JSON file), a
+        pick stored there for the same GPU, library build, grid and view
+        sizes is applied without timing; a new pick is added to the file."""
         import torch
+        key = tune_key(self, views) if cache else None
+        if cache:
+            got = _read_tune_cache(cache).get(key)
+            if got is not None:
+                opts = lfp.lfp_render_opts()
+                opts.engine, opts.schedule, opts.occupancy = got["engine"], got["schedule"], got["occupancy"]
+                opts.tile_w, opts.tile_h = got["tile"]
+                lfp.lfp_set_defaults(self.handle, opts)
+                return dict(got, tile=tuple(got["tile"]), cached=True)
         arr, n, total = make_views(views)
         dev = torch.device("cuda", torch.cuda.current_device())
         rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
@@ -193,7 +250,10 @@ class ProbeGrid:
         o = lfp.lfp_outputs()
         o.rgb, o.cls = rgb.data_ptr(), cls.data_ptr()
         b = lfp.lfp_autotune(self.handle, arr, n, o, _stream_handle(stream))
-        return {"engine": b.engine, "tile": (b.tile_w, b.tile_h), "schedule": b.schedule, "occupancy": b.occupancy}
+        pick = {"engine": b.engine, "tile": (b.tile_w, b.tile_h), "schedule": b.schedule, "occupancy": b.occupancy}
+        if cache:
+            _write_tune_cache(cache, key, pick)
+        return pick
 
     def render_graph(self, views, aux=False, engine=0, occupancy=0, stream=None):
         """Capture one render of these views in a CUDA graph (outputs are

@@ -628,6 +628,23 @@ lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const l
     return LFP_OK;
 }
 
+lfp_status lfp_set_defaults(lfp_grid* g, const lfp_render_opts* o) {
+    if (!g || !o) return LFP_ERR_INVALID_ARG;
+    if (o->engine < LFP_ENGINE_AUTO || o->engine > LFP_ENGINE_NESTED) return LFP_ERR_INVALID_ARG;
+    if (o->occupancy < LFP_OCC_AUTO || o->occupancy > LFP_OCC_9) return LFP_ERR_INVALID_ARG;
+    if (o->schedule < LFP_SCHED_AUTO || o->schedule > LFP_SCHED_PERSISTENT) return LFP_ERR_INVALID_ARG;
+    if ((o->tile_w || o->tile_h) && !valid_tile(o->tile_w, o->tile_h)) return LFP_ERR_INVALID_ARG;
+    if (o->march != LFP_MARCH_HIER) return LFP_ERR_INVALID_ARG;  // the flat march is a per-call diagnostic
+    if (o->engine != LFP_ENGINE_AUTO) g->engine = o->engine;
+    if (o->occupancy != LFP_OCC_AUTO) g->stream_occ = o->occupancy == LFP_OCC_9 ? 1 : 0;
+    if (o->tile_w) {
+        g->tile_w = o->tile_w;
+        g->tile_h = o->tile_h;
+    }
+    if (o->schedule != LFP_SCHED_AUTO) g->schedule = o->schedule;
+    return LFP_OK;
+}
+
 lfp_status lfp_render_to_host(lfp_grid* g, const lfp_view* views, int n_views, float* rgb_host, uint8_t* cls_host,
                               void* stream) {
     if (!g) return LFP_ERR_INVALID_ARG;

@@ -89,6 +89,7 @@ def _load():
         "lfp_sync_host": ([vp], i),
         "lfp_render_static": ([vp, P(lfp_view), i, P(lfp_outputs), vp], i),
         "lfp_autotune": ([vp, P(lfp_view), i, P(lfp_outputs), P(lfp_render_opts), vp], i),
+        "lfp_set_defaults": ([vp, P(lfp_render_opts)], i),
         "lfp_render_backward": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, vp], i),
         "lfp_render_backward_ex": ([vp, P(lfp_view), i, vp, vp, vp, vp, vp, i, vp], i),
         "lfp_build_probes_from_points": ([vp, i, i, P(lfp_point_cloud), ctypes.c_float, vp], i),
@@ -155,6 +156,11 @@ def lfp_autotune(grid, views, n_views, outputs: lfp_outputs, stream) -> lfp_rend
     best = lfp_render_opts()
     _check(_lib.lfp_autotune(grid, views, n_views, ctypes.byref(outputs), ctypes.byref(best), stream), "lfp_autotune")
     return best
+
+
+def lfp_set_defaults(grid, opts: lfp_render_opts) -> None:
+    """Make opts the grid's default launch configuration."""
+    _check(_lib.lfp_set_defaults(grid, ctypes.byref(opts)), "lfp_set_defaults")
 
 
 def lfp_render_to_host(grid, views, n_views, rgb_host, cls_host, stream) -> None:

@@ -1,6 +1,7 @@
-"""Host logic of bench.py that needs no GPU: which committed ncu summary a
+"""Host logic that needs no GPU: in bench.py, which committed ncu summary a
 launch may use (source hash, register budget), the issue roofline arithmetic
-and the algorithmic-bytes model of the fetch counters."""
+and the algorithmic-bytes model of the fetch counters; in the binding, the
+autotuner cache's key and file."""
 import json
 
 import pytest
@@ -85,3 +86,30 @@ def test_committed_summaries_parse():
             entries = [d]
         for e in entries:
             assert ("warp_inst_per_launch" in e) or ("warp_inst_per_ray" in e), f
+
+
+def test_autotune_cache_key_and_file(tmp_path):
+    """The autotuner's cache key names the GPU, the library build, the grid
+    descriptor and the multiset of view sizes; picks round-trip through the
+    JSON file."""
+    import types
+    import paper_2507_14624_gb300 as lfpk
+    from paper_2507_14624_gb300 import lfp
+    d = lfp.lfp_grid_desc()
+    d.nx, d.ny, d.nz, d.spacing, d.N, d.M = 4, 4, 4, 0.5, 256, 16
+    grid = types.SimpleNamespace(desc=d)
+    V = lambda w, h: types.SimpleNamespace(W=w, H=h)  # noqa: E731
+    k1 = lfpk.tune_key(grid, [V(64, 48), V(32, 32)], "GB300")
+    assert k1 == lfpk.tune_key(grid, [V(32, 32), V(64, 48)], "GB300")  # order does not matter
+    assert k1 != lfpk.tune_key(grid, [V(64, 48), V(32, 33)], "GB300")
+    assert k1 != lfpk.tune_key(grid, [V(64, 48), V(32, 32)], "B200")
+    d2 = lfp.lfp_grid_desc()
+    d2.nx, d2.ny, d2.nz, d2.spacing, d2.N, d2.M = 4, 4, 4, 0.5, 256, 32
+    assert k1 != lfpk.tune_key(types.SimpleNamespace(desc=d2), [V(64, 48), V(32, 32)], "GB300")
+    path = str(tmp_path / "tune.json")
+    pick = {"engine": 2, "tile": (16, 8), "schedule": 2, "occupancy": 0}
+    lfpk._write_tune_cache(path, k1, pick)
+    lfpk._write_tune_cache(path, "other", dict(pick, engine=1))
+    got = lfpk._read_tune_cache(path)
+    assert got[k1] == {"engine": 2, "tile": [16, 8], "schedule": 2, "occupancy": 0}
+    assert got["other"]["engine"] == 1

@@ -108,3 +108,21 @@ def test_batched_workload_full_size_sampled_against_oracle():
     assert st["class_match"] >= 0.999 and st["disagree"] <= 2e-3, st
     assert st["max_err"] <= 1e-3, st
     g.close()
+
+
+def test_autotune_cache_applies_the_stored_pick(tmp_path):
+    """A second grid of the same configuration takes the pick from the cache
+    file without timing and renders exactly as the tuned grid does."""
+    lfpk, sc, views, g = _grid("tiny")
+    vs = _mixed_views(sc, 4)
+    path = str(tmp_path / "tune.json")
+    first = g.autotune(vs, cache=path)
+    assert "cached" not in first
+    a = g.render(vs, hit_texel=True)
+    lfpk2, sc2, views2, h = _grid("tiny")
+    second = h.autotune(vs, cache=path)
+    assert second.get("cached") is True
+    assert {k: second[k] for k in first} == first
+    b = h.render(vs, hit_texel=True)
+    for k in ("cls", "probe", "texel", "rgb"):
+        assert torch.equal(a[k], b[k]), k
