@@ -126,3 +126,13 @@ def test_allocation_fault_injection_returns_oom_without_a_device(lib):
     assert out.returncode == 0, out.stderr
     st, h = out.stdout.split()
     assert int(st) == 2 and h == "None"
+
+
+def test_checked_library_exports_the_same_entry_points(lib):
+    """liblfp_checked.so (every texel index tested) is a drop-in for
+    liblfp.so: it exports every entry point the header declares."""
+    import __graft_entry__
+    path = __graft_entry__._cuda_build_module().build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (lfp_\w+)", out))
+    assert set(declared_functions()) <= exported
