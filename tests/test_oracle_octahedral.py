@@ -92,3 +92,53 @@ def test_bilinear_taps_at_texel_centre_are_exact():
         k = int(np.argmax(w))
         assert (ti[k], tj[k]) == (i, j) and abs(w[k] - 1.0) < 1e-12
         assert abs(w.sum() - 1.0) < 1e-12
+
+
+GOLDEN_TAPS = os.path.join(os.path.dirname(__file__), "golden", "bilinear_taps.txt")
+
+
+def _golden_taps():
+    rows = []
+    for line in open(GOLDEN_TAPS):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        lhs, rhs = line.split("|")
+        N, u, v = lhs.split()
+        taps = [tuple(t.split()) for t in rhs.split(";")]
+        rows.append((int(N), (float(u), float(v)),
+                     [(int(i), int(j), float(w)) for i, j, w in taps]))
+    return rows
+
+
+def test_bilinear_taps_match_hand_derived_table():
+    """Taps and weights off texel centres, at the mirror border and past the
+    corners, against the table derived by hand in tests/golden/bilinear_taps.txt."""
+    rows = _golden_taps()
+    assert len(rows) >= 6
+    for N, uv, want in rows:
+        ti, tj, w = oracle.bilinear_taps(N, uv)
+        for k, (i, j, wk) in enumerate(want):
+            assert (ti[k], tj[k]) == (i, j), (N, uv, k)
+            assert abs(w[k] - wk) <= 1e-15, (N, uv, k)
+
+
+def test_bilinear_reproduces_affine_maps_off_centre():
+    """Bilinear interpolation over texel centres reproduces an affine function
+    of the texel coordinate exactly: with c(i, j) = alpha + beta i + gamma j
+    stored at the centres, the lookup at uv returns alpha + beta s + gamma t,
+    s = u N - 0.5, t = v N - 0.5, wherever all four taps lie inside the map.
+    beta != gamma, so exchanging the two fractions, or a weight with its
+    complement, moves the result by a multiple of |beta - gamma| or more."""
+    rng = np.random.default_rng(21)
+    for N in (4, 16, 64):
+        alpha, beta, gamma = rng.uniform(-1, 1, 3), rng.uniform(0.5, 2, 3), rng.uniform(-3, -0.5, 3)
+        jj, ii = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+        c = alpha + beta * ii[..., None] + gamma * jj[..., None]  # [j][i][3]
+        uv = rng.uniform(0.5 / N, (N - 0.5) / N, (400, 2))
+        for u, v in uv:
+            ti, tj, w = oracle.bilinear_taps(N, (u, v))
+            got = (w[:, None] * c[tj, ti]).sum(0)
+            want = alpha + beta * (u * N - 0.5) + gamma * (v * N - 0.5)
+            assert np.max(np.abs(got - want)) <= 1e-12
+            assert abs(w.sum() - 1.0) <= 1e-15 and np.all(w >= 0)

@@ -213,3 +213,86 @@ def test_trace_one_probe_in_an_empty_cube_room():
             want = np.clip(np.floor((p + 1) / 2 * g.N).astype(int), 0, g.N - 1)
             assert _within_one_texel(g.N, [tex], [want])[0]
         assert n_hit >= 250
+
+
+def _sphere_maps(g, R, w):
+    """Every probe stores distance R in every texel (a sphere of radius R
+    around it) and the normal -w for one ray direction w, so a crossing by a
+    ray along w always passes the normal test."""
+    P, N = g.n_probes, g.N
+    d = np.full((P, N, N), R, np.float32)
+    n = np.broadcast_to(-np.asarray(w, np.float32), (P, N, N, 3)).copy()
+    r = np.zeros((P, N, N, 3), np.float32)
+    return d, n, r
+
+
+def _roots(Y0, w, R):
+    """Both roots of |Y0 + t w| = R (|w| = 1), in the cancellation-free forms."""
+    B = float(np.dot(Y0, w))
+    C = float(np.dot(Y0, Y0)) - R * R
+    disc = B * B - C
+    s = np.sqrt(max(disc, 0.0))
+    if B > 0:
+        q = -(B + s)
+        return C / q, q
+    q = s - B
+    return C / q if q != 0 else -B, q
+
+
+@pytest.mark.parametrize("case", ["in_front", "behind_approaching", "behind_receding", "never_reaches"])
+def test_hit_point_is_the_analytic_root(case):
+    """Hit point inside the deciding texel (the reading of the paper's
+    highResolutionTracing, which returns only the texel): against a probe
+    whose map holds a sphere of radius R, traceOneProbe returns
+      - a ray starting inside the sphere: the larger root of |X + t w - O| = R;
+      - starting just outside and approaching: the smaller root;
+      - starting just outside and receding: the segment start t = 0;
+      - approaching but passing the probe at more than R: the closest
+        approach -(X - O).w.
+    Closed forms to 1e-9; exchanging the two roots fails the first two cases."""
+    g = synth.Grid(2, 2, 2, 1.0, 64, 16)
+    R = 0.375
+    O = g.probe_positions()[5]
+    rng = np.random.default_rng({"in_front": 1, "behind_approaching": 2, "behind_receding": 3,
+                                 "never_reaches": 4}[case])
+    for _ in range(40):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        v = rng.normal(size=3)
+        v -= np.dot(v, u) * u
+        v /= np.linalg.norm(v)
+        if case == "in_front":
+            Y0 = rng.uniform(0.05, 0.9) * R * u
+            w = rng.normal(size=3)
+        elif case == "behind_approaching":
+            Y0 = R * (1 + 1e-3) * u
+            w = -u + rng.uniform(-0.3, 0.3) * v  # mostly towards the probe: reaches R at once
+        elif case == "behind_receding":
+            Y0 = R * (1 + 1e-3) * u
+            w = u + rng.uniform(-0.5, 0.5) * v
+        else:
+            Y0 = R * (1 + 1e-2) * u
+            w = v - 1e-4 * u  # nearly tangent, approaching: closest approach just above R
+        w = w / np.linalg.norm(w)
+        X = O + Y0
+        d, n, r = _sphere_maps(g, R, w)
+        o = oracle.Oracle(g, d, n, r)
+        cls, tex, uv, th = o.trace_one_probe(5, X, w, 0.0, np.inf)
+        assert cls == oracle.HIT
+        small, large = sorted(_roots(Y0, w, R))
+        B = float(np.dot(Y0, w))
+        if case == "in_front":
+            want = large
+        elif case == "behind_approaching":
+            assert B * B - (np.dot(Y0, Y0) - R * R) > 0
+            want = small
+        elif case == "behind_receding":
+            assert B > 0
+            want = 0.0
+        else:
+            assert B * B - (np.dot(Y0, Y0) - R * R) < 0 and B < 0
+            want = -B
+        assert abs(th - want) <= 1e-9, (case, th, want)
+        if case != "behind_receding":  # the point found lies on the ray at the expected radius
+            rad = np.linalg.norm(Y0 + th * w)
+            assert abs(rad - (R if case != "never_reaches" else np.sqrt(np.dot(Y0, Y0) - B * B))) <= 1e-9
