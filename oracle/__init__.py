@@ -83,7 +83,7 @@ def _load():
             "orc_backward": ([G, ll, vp, vp, vp, vp, vp], None),
             "orc_bilinear_taps": ([i, vp, vp, vp, vp], None),
             "orc_num_threads": ([], i),
-            "orc_splat_probes": ([ll, vp, vp, vp, i, vp, i, ctypes.c_float, vp, vp, vp], None),
+            "orc_splat_probes": ([ll, vp, vp, vp, i, vp, i, ctypes.c_float, vp, vp, vp, vp, vp, vp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -362,13 +362,17 @@ class Hierarchy:
 # probe maps from a point cloud
 # ---------------------------------------------------------------------------
 
-def splat_probes(xyz, rgb, probe_pos, N, normal=None, empty_dist=0.0):
+def splat_probes(xyz, rgb, probe_pos, N, normal=None, empty_dist=0.0, details=False):
     """Probe maps from a point cloud (Sec. 4.1 simulated probes, Sec. 5.1
-    probe data generation): per probe and texel the point nearest to the
-    probe; texel binning and ranking in float32 (see lfp_oracle.c).
-    xyz, rgb, normal: [n][3]; probe_pos [P][3]. Returns float32 dist
-    [P][N][N], normal [P][N][N][3] (the points' normals, or the incoming
-    direction -v/|v| when normal is None), radiance [P][N][N][3]."""
+    probe data generation), in double precision: per probe and texel the
+    point nearest to the probe (ties to the lower point index); see
+    lfp_oracle.c. xyz, rgb, normal: [n][3]; probe_pos [P][3]. Returns float32
+    dist [P][N][N], normal [P][N][N][3] (the points' normals, or the incoming
+    direction -v/|v| when normal is None), radiance [P][N][N][3]; with
+    details=True also a dict: winner [P][N][N] int64 (-1 empty), decided
+    [P][N][N] bool (float32 rounding of the builder's recipe cannot change
+    the winner), dcand [P][N][N] float32 (least distance of a point that
+    float32 rounding can put into the texel, inf if none)."""
     lib = _load()
     xyz = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
     rgb = np.ascontiguousarray(rgb, np.float32).reshape(-1, 3)
@@ -378,6 +382,13 @@ def splat_probes(xyz, rgb, probe_pos, N, normal=None, empty_dist=0.0):
     dist = np.empty((P, N, N), np.float32)
     nout = np.empty((P, N, N, 3), np.float32)
     rad = np.empty((P, N, N, 3), np.float32)
+    win = dec = dc = None
+    if details:
+        win = np.empty((P, N, N), np.int64)
+        dec = np.empty((P, N, N), np.uint8)
+        dc = np.empty((P, N, N), np.float32)
     lib.orc_splat_probes(ctypes.c_longlong(len(xyz)), _p(xyz), _p(rgb), _p(nrm), P, _p(pos), N,
-                         ctypes.c_float(empty_dist), _p(dist), _p(nout), _p(rad))
+                         ctypes.c_float(empty_dist), _p(dist), _p(nout), _p(rad), _p(win), _p(dec), _p(dc))
+    if details:
+        return dist, nout, rad, {"winner": win, "decided": dec.astype(bool), "dcand": dc}
     return dist, nout, rad

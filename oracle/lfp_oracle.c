@@ -854,72 +854,85 @@ int orc_num_threads(void) {
 
 /* ---------------------------------------------------------------------
  * Probe maps from a point cloud (Sec. 4.1, simulated probe data; Sec. 5.1,
- * probe data generation): every point is taken into the probe's frame
- * (v = p - O) and projected onto the octahedral map; per texel the point
- * nearest to the probe is kept. Distance = |v|, radiance = that point's
- * colour, normal = its normal when the cloud has normals, else the incoming
- * direction -v / |v| (R8). A texel no point reaches gets distance empty_dist,
- * radiance 0 and minus its texel-centre direction.
+ * probe data generation), the plain definition in double precision. Every
+ * point p is taken into the probe's frame, v = p - O, and onto the
+ * octahedral map (R1, orc_oct_encode); its texel is (floor(u N), floor(w N))
+ * of the square coordinate (u, w) = (enc(v) + 1) / 2, clamped to [0, N - 1].
+ * Per texel the point nearest to the probe wins: smallest |v|^2, ties to the
+ * lower point index. Distance = |v|, radiance = that point's colour, normal =
+ * its normal when the cloud has normals, else the incoming direction
+ * -v / |v| (R8). A texel no point reaches gets distance empty_dist, radiance
+ * 0 and minus its texel-centre direction. A point at the probe (v = 0) has
+ * no direction and is skipped. OpenMP over probes.
  *
- * The texel a point lands in and the ranking of points are integer decisions
- * made from floating point, so they are taken in float32 with this exact
- * sequence of correctly rounded operations (no fused multiply-add), the
- * precision the GPU builder decides in:
- *   v = p - O per component; q = (v.x*v.x + v.y*v.y) + v.z*v.z;
- *   s = (|v.x| + |v.y|) + |v.z|, a point with s = 0 or a non-finite q or s is
- *   skipped; r = 1 / s; px = v.x r, py = v.y r; if v.z < 0:
- *   (px, py) = ((1 - |py|) sgn px, (1 - |px|) sgn py) with sgn 0 = +1;
- *   i = floor((px + 1) * (N / 2)) clamped to [0, N - 1], likewise j from py;
- *   the smallest q wins, ties to the lower point index; distance = sqrt(q).
- * OpenMP over probes; each probe keeps its own winner table.
+ * Optional outputs for comparing a float32 implementation with it (any may
+ * be NULL):
+ *   winner  [P][N][N]  the winning point's index, -1 for an empty texel;
+ *   decided [P][N][N]  1 where float32 rounding cannot change the winner,
+ *                      0 where it can (see below);
+ *   dcand   [P][N][N]  the least |v| over the points that float32 rounding
+ *                      can put into the texel (+inf: none).
+ * The margins follow from counting correctly rounded float32 operations
+ * (unit roundoff 2^-24) in the recipe the GPU builder documents (v = p - O,
+ * |v|^2 from three products and two sums; |v|_1 from two sums, one
+ * reciprocal, two products, the fold, then (p + 1) N / 2): the texel
+ * coordinate moves by at most 5.5 N 2^-24 texel widths, |v|^2 by at most
+ * 5 2^-24 relative. With margins du = 8 N 2^-24 and dq = 16 2^-24, a point is
+ * "near" a texel when it lies within du of it; a texel is undecided when a
+ * point near one of its boundaries (inside or outside) is no farther than
+ * its winner within dq (or the texel is empty), or when a second point
+ * inside it ties with the winner within dq.
  */
-static int splat_bin(const float p[3], const float O[3], int N, float* q_out, float v_out[3]) {
-    float vx = p[0] - O[0], vy = p[1] - O[1], vz = p[2] - O[2];
-    float q = vx * vx + vy * vy;
-    q = q + vz * vz;
-    float s = fabsf(vx) + fabsf(vy);
-    s = s + fabsf(vz);
-    if (!(s > 0.0f) || !isfinite(s) || !isfinite(q)) return -1;
-    float inv = 1.0f / s;
-    float px = vx * inv, py = vy * inv;
-    if (vz < 0.0f) {
-        float fx = (1.0f - fabsf(py)) * (px >= 0.0f ? 1.0f : -1.0f);
-        float fy = (1.0f - fabsf(px)) * (py >= 0.0f ? 1.0f : -1.0f);
-        px = fx;
-        py = fy;
+static int splat_texel(const float p[3], const float O[3], int N, double* q, double v[3], double u[2]) {
+    for (int a = 0; a < 3; ++a) v[a] = (double)p[a] - (double)O[a];
+    double qq = dot3(v, v);
+    double s = fabs(v[0]) + fabs(v[1]) + fabs(v[2]);
+    if (!(s > 0.0) || !isfinite(s) || !isfinite(qq)) return -1;
+    double e[2];
+    orc_oct_encode(v, e);
+    int ij[2];
+    for (int a = 0; a < 2; ++a) {
+        u[a] = (e[a] + 1.0) * 0.5 * N;
+        int i = (int)floor(u[a]);
+        ij[a] = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
     }
-    float half = (float)(N / 2);
-    int i = (int)floorf((px + 1.0f) * half), j = (int)floorf((py + 1.0f) * half);
-    i = i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
-    j = j < 0 ? 0 : (j > N - 1 ? N - 1 : j);
-    *q_out = q;
-    v_out[0] = vx;
-    v_out[1] = vy;
-    v_out[2] = vz;
-    return i + N * j;
+    *q = qq;
+    return ij[0] + N * ij[1];
+}
+
+static int clamp_index(double x, int N) {
+    int i = (int)floor(x);
+    return i < 0 ? 0 : (i > N - 1 ? N - 1 : i);
 }
 
 void orc_splat_probes(long long n_points, const float* xyz, const float* rgb, const float* nrm, int n_probes,
                       const float* probe_pos, int N, float empty_dist, float* dist, float* normal,
-                      float* radiance) {
+                      float* radiance, long long* winner, unsigned char* decided, float* dcand) {
     const long long NN = (long long)N * N;
+    const double eps32 = ldexp(1.0, -24);
+    const double du = 8.0 * N * eps32, dq = 16.0 * eps32;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int p = 0; p < n_probes; ++p) {
-        uint64_t* best = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)NN);
-        for (long long t = 0; t < NN; ++t) best[t] = UINT64_MAX;
+        double* bq = (double*)malloc(sizeof(double) * (size_t)NN);
+        long long* bk = (long long*)malloc(sizeof(long long) * (size_t)NN);
+        for (long long t = 0; t < NN; ++t) {
+            bq[t] = INFINITY;
+            bk[t] = -1;
+        }
         const float* O = probe_pos + 3 * p;
         for (long long k = 0; k < n_points; ++k) {
-            float q, v[3];
-            int t = splat_bin(xyz + 3 * k, O, N, &q, v);
+            double q, v[3], u[2];
+            int t = splat_texel(xyz + 3 * k, O, N, &q, v, u);
             if (t < 0) continue;
-            uint32_t qb;
-            memcpy(&qb, &q, 4);
-            uint64_t key = ((uint64_t)qb << 32) | (uint64_t)(uint32_t)k;
-            if (key < best[t]) best[t] = key;
+            if (q < bq[t]) { /* points come in index order: an equal q keeps the lower index */
+                bq[t] = q;
+                bk[t] = k;
+            }
         }
         for (long long t = 0; t < NN; ++t) {
             long long o = (long long)p * NN + t;
-            if (best[t] == UINT64_MAX) {
+            if (winner) winner[o] = bk[t];
+            if (bk[t] < 0) {
                 double pp[2] = {((t % N) + 0.5) / N * 2.0 - 1.0, ((t / N) + 0.5) / N * 2.0 - 1.0}, d[3];
                 orc_oct_decode(pp, d);
                 dist[o] = empty_dist;
@@ -929,16 +942,50 @@ void orc_splat_probes(long long n_points, const float* xyz, const float* rgb, co
                 }
                 continue;
             }
-            long long k = (long long)(best[t] & 0xffffffffu);
-            float q, v[3];
-            splat_bin(xyz + 3 * k, O, N, &q, v);
-            float r = sqrtf(q);
-            dist[o] = r;
+            long long k = bk[t];
+            double q, v[3], u[2];
+            splat_texel(xyz + 3 * k, O, N, &q, v, u);
+            double r = sqrt(q);
+            dist[o] = (float)r;
             for (int a = 0; a < 3; ++a) {
-                normal[3 * o + a] = nrm ? nrm[3 * k + a] : -v[a] / r;
+                normal[3 * o + a] = nrm ? nrm[3 * k + a] : (float)(-v[a] / r);
                 radiance[3 * o + a] = rgb[3 * k + a];
             }
         }
-        free(best);
+        if (decided || dcand) {
+            unsigned char* dec = (unsigned char*)malloc((size_t)NN);
+            double* cq = (double*)malloc(sizeof(double) * (size_t)NN);
+            for (long long t = 0; t < NN; ++t) {
+                dec[t] = 1;
+                cq[t] = bq[t];
+            }
+            for (long long k = 0; k < n_points; ++k) {
+                double q, v[3], u[2];
+                int t = splat_texel(xyz + 3 * k, O, N, &q, v, u);
+                if (t < 0) continue;
+                int ia = clamp_index(u[0] - du, N), ib = clamp_index(u[0] + du, N);
+                int ja = clamp_index(u[1] - du, N), jb = clamp_index(u[1] + du, N);
+                if (ia == ib && ja == jb) { /* the point stays in its texel */
+                    if (k != bk[t] && q <= bq[t] * (1.0 + dq)) dec[t] = 0;
+                    continue;
+                }
+                int is[2] = {ia, ib}, js[2] = {ja, jb};
+                for (int x = 0; x < 2; ++x)
+                    for (int y = 0; y < 2; ++y) {
+                        long long tt = is[x] + (long long)N * js[y];
+                        if (bk[tt] < 0 || q <= bq[tt] * (1.0 + dq)) dec[tt] = 0;
+                        if (q < cq[tt]) cq[tt] = q;
+                    }
+            }
+            for (long long t = 0; t < NN; ++t) {
+                long long o = (long long)p * NN + t;
+                if (decided) decided[o] = dec[t];
+                if (dcand) dcand[o] = isinf(cq[t]) ? INFINITY : (float)sqrt(cq[t]);
+            }
+            free(dec);
+            free(cq);
+        }
+        free(bq);
+        free(bk);
     }
 }

@@ -1,7 +1,18 @@
 """GPU point-cloud probe builder (lfp_build_probes_from_points, through the C
-ABI) against the oracle's splat: the texel binning and the ranking are
-integer decisions taken in float32 on both sides, so distances and colours
-must match exactly; normals pass through the octahedral storage (<= 2e-6)."""
+ABI) against the oracle's splat, the plain double-precision definition of
+Sec. 4.1 / 5.1 (nearest point per texel).
+
+The texel a point lands in and the ranking are integer decisions that the GPU
+takes in float32. The oracle marks every texel whose winner float32 rounding
+of the builder's documented recipe could change ("undecided": a contested
+point within 8 N 2^-24 texel widths of a boundary, or a tie within 16 2^-24
+in |v|^2). On every decided texel the GPU must hold the oracle's winner:
+the same colour, the distance within ULP_TOL float32 ulps (|v|^2 carries at
+most five roundings, 2.5 ulp after the square root, plus the final rounding
+on each side), the normal within NRM_TOL (double vs float32 direction plus
+the octahedral storage). On undecided texels the GPU's result must be valid:
+empty, or no nearer than the nearest point that float32 rounding can put
+there. Each test states the shares it saw."""
 import numpy as np
 import pytest
 
@@ -24,8 +35,40 @@ def _cloud(name="tiny", n_dirs=300000, scans=4):
     return _CACHE[key]
 
 
+ULP_TOL = 4
+NRM_TOL = 3e-6
+
+
 def _read(g):
     return [t.cpu().numpy() for t in g.read_probes()]
+
+
+def check_built_maps(got, want, det, empty_dist=0.0, rad_f16=False, nrm_tol=NRM_TOL, label=""):
+    """Decided texels: the oracle's winner; undecided: a valid result. Returns the shares."""
+    d, n, r = got
+    od, on, orad = want
+    dec = det["decided"]
+    filled = det["winner"] >= 0
+    rr = orad.astype(np.float16).astype(np.float32) if rad_f16 else orad
+    # decided and filled: same winner
+    m = dec & filled
+    ulp = np.spacing(od[m])
+    assert np.all(np.abs(d[m] - od[m]) <= ULP_TOL * ulp), label
+    assert np.array_equal(r[m], rr[m]), label
+    assert np.abs(n[m] - on[m]).max() <= nrm_tol, label
+    # decided and empty: empty on the GPU too
+    e = dec & ~filled
+    assert np.all(d[e] == empty_dist) and np.all(r[e] == 0), label
+    # undecided: empty, or no nearer than the nearest candidate point
+    u = ~dec
+    ok = (d[u] == empty_dist) | (d[u].astype(np.float64) >= det["dcand"][u].astype(np.float64) * (1 - 8 * 2.0 ** -24))
+    assert np.all(ok), label
+    differ = (np.abs(d - od) > ULP_TOL * np.spacing(np.maximum(od, 1e-30))) | np.any(r != rr, axis=-1)
+    st = {"texels": int(dec.size), "undecided": float(1 - dec.mean()), "differ": float(differ.mean()),
+          "within_1ulp": float((np.abs(d[m] - od[m]) <= np.spacing(od[m])).mean())}
+    print(label, st)
+    assert st["undecided"] <= 0.02, label
+    return st
 
 
 @pytest.mark.parametrize("with_normals", [False, True])
@@ -36,11 +79,9 @@ def test_built_maps_equal_oracle_splat(with_normals):
     g = lfpk.ProbeGrid(sc.grid)
     g.build_from_points(pc["xyz"], pc["rgb"], nrm, empty_dist=0.0)
     d, n, r = _read(g)
-    rd, rn, rr = oracle.splat_probes(pc["xyz"], pc["rgb"], sc.grid.probe_positions(), sc.grid.N, normal=nrm,
-                                     empty_dist=0.0)
-    assert np.array_equal(d, rd)
-    assert np.array_equal(r, rr)
-    assert np.abs(n - rn).max() <= 2e-6
+    *want, det = oracle.splat_probes(pc["xyz"], pc["rgb"], sc.grid.probe_positions(), sc.grid.N, normal=nrm,
+                                     empty_dist=0.0, details=True)
+    check_built_maps((d, n, r), want, det, label=f"tiny scan, normals={with_normals}")
     assert (d == 0).mean() < 0.05  # a few texels no scan reached
 
 
@@ -79,8 +120,8 @@ def test_render_from_built_probes_matches_oracle():
 
 def test_chunked_build_with_fp16_texels():
     """40 probes at N = 512: the (distance, index) table of all probes is
-    80 MiB, so the build runs in two chunks; FP16 radiance comes back as the
-    oracle's colours rounded to half precision."""
+    80 MiB, so the build runs in two chunks; on decided texels FP16 radiance
+    comes back as the oracle's colours rounded to half precision."""
     import paper_2507_14624_gb300 as lfpk
     g = synth.Grid(5, 4, 2, 0.25, 512, 32)
     sc = synth.make_scene(g, 12, 4, [1.0], seed=31)
@@ -88,10 +129,9 @@ def test_chunked_build_with_fp16_texels():
     grid = lfpk.ProbeGrid(g, radiance_fmt=lfpk.LFP_TEXEL_F16, normal_fmt=lfpk.LFP_TEXEL_F16)
     grid.build_from_points(pc["xyz"], pc["rgb"], empty_dist=0.0)
     d, n, r = _read(grid)
-    rd, rn, rr = oracle.splat_probes(pc["xyz"], pc["rgb"], g.probe_positions(), g.N, empty_dist=0.0)
-    assert np.array_equal(d, rd)
-    assert np.array_equal(r, rr.astype(np.float16).astype(np.float32))
-    assert np.abs(n - rn).max() <= 2e-3  # half-precision octahedral pair
+    *want, det = oracle.splat_probes(pc["xyz"], pc["rgb"], g.probe_positions(), g.N, empty_dist=0.0, details=True)
+    check_built_maps((d, n, r), want, det, rad_f16=True, nrm_tol=2e-3,  # half-precision octahedral pair
+                     label="chunked N=512, FP16 texels")
 
 
 def test_build_refuses_bad_ranges():
@@ -108,8 +148,8 @@ def test_build_refuses_bad_ranges():
 def test_full_size_build_workload_equals_oracle_splat():
     """The build configuration the bench times: the room grid (64 probes,
     N=256) from 4 scans of 2^23 directions each (33.5 M points), device-
-    resident cloud, one call for all probes; distances and colours equal to
-    the oracle's splat, normals within the octahedral storage error."""
+    resident cloud, one call for all probes, against the double-precision
+    oracle under the decided-texel rule."""
     import paper_2507_14624_gb300 as lfpk
     sc, views = synth.workload("room")
     pc = synth.scan(sc, synth.scan_positions(sc, 4, 2024), 1 << 23, seed=2025)
@@ -118,8 +158,6 @@ def test_full_size_build_workload_equals_oracle_splat():
     xyz, rgb = (torch.tensor(pc[k], device="cuda") for k in ("xyz", "rgb"))
     g.build_from_points(xyz, rgb)
     d, n, r = _read(g)
-    rd, rn, rr = oracle.splat_probes(pc["xyz"], pc["rgb"], sc.grid.probe_positions(), sc.grid.N)
-    assert np.array_equal(d, rd)
-    assert np.array_equal(r, rr)
-    assert np.abs(n - rn).max() <= 2e-6
+    *want, det = oracle.splat_probes(pc["xyz"], pc["rgb"], sc.grid.probe_positions(), sc.grid.N, details=True)
+    check_built_maps((d, n, r), want, det, label="room, 33.5 M points")
     g.close()

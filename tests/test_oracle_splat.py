@@ -53,41 +53,128 @@ def test_nearer_shell_occludes_the_farther_one_and_holes_stay_empty():
     assert np.all(d[0][dirs[..., 2] > 0.3] > 0)
 
 
+def _texel_fp64(pts, O, N):
+    """Texel of each point through the pinned octahedral encoder: floor of
+    the square coordinate (enc(v) + 1) / 2 * N, clamped."""
+    v = pts.astype(np.float64) - O.astype(np.float64)
+    p = oracle.oct_encode(v)
+    ij = np.clip(np.floor((p + 1.0) * 0.5 * N).astype(np.int64), 0, N - 1)
+    return ij[:, 0] + N * ij[:, 1], (v * v).sum(1)
+
+
 def test_brute_force_nearest_point_per_texel_with_ties():
-    """Tiny cloud, every texel's winner found by a Python loop over points
-    (float32 binning as the builder states it); duplicated points make exact
-    ties, which the lower point index wins."""
+    """Tiny cloud: every texel's winner from a sort of (texel, |v|^2, index)
+    over all points; duplicated points make exact ties, which the lower point
+    index wins."""
     rng = np.random.default_rng(4)
     N = 4
     pts = rng.uniform(-1, 1, (300, 3)).astype(np.float32)
     pts = np.concatenate([pts, pts[:40]])  # indices 300.. duplicate 0..39
     rgb = rng.uniform(0, 1, (len(pts), 3)).astype(np.float32)
     probes = np.float32([[0.05, -0.1, 0.2], [0.3, 0.3, -0.4]])
-    d, n, r = oracle.splat_probes(pts, rgb, probes, N, empty_dist=-1.0)
-    f = np.float32
+    d, n, r, x = oracle.splat_probes(pts, rgb, probes, N, empty_dist=-1.0, details=True)
     for p, O in enumerate(probes):
-        best = {}
-        for k, x in enumerate(pts):
-            v = x - O
-            q = f(f(v[0] * v[0]) + f(v[1] * v[1]))
-            q = f(q + f(v[2] * v[2]))
-            s = f(f(abs(v[0]) + abs(v[1])) + abs(v[2]))
-            inv = f(f(1) / s)
-            px, py = f(v[0] * inv), f(v[1] * inv)
-            if v[2] < 0:
-                px, py = (f((f(1) - abs(py)) * (1 if px >= 0 else -1)), f((f(1) - abs(px)) * (1 if py >= 0 else -1)))
-            i = min(max(int(np.floor(f((px + f(1)) * f(N / 2)))), 0), N - 1)
-            j = min(max(int(np.floor(f((py + f(1)) * f(N / 2)))), 0), N - 1)
-            if (j, i) not in best or (q, k) < best[(j, i)]:
-                best[(j, i)] = (q, k)
-        for j in range(N):
-            for i in range(N):
-                if (j, i) in best:
-                    q, k = best[(j, i)]
-                    assert k < 300
-                    assert d[p, j, i] == np.sqrt(q) and np.array_equal(r[p, j, i], rgb[k])
-                else:
-                    assert d[p, j, i] == -1.0
+        t, q = _texel_fp64(pts, O, N)
+        order = np.lexsort((np.arange(len(pts)), q, t))  # by texel, then |v|^2, then index
+        first = np.ones(len(order), bool)
+        first[1:] = t[order][1:] != t[order][:-1]
+        win = np.full(N * N, -1)
+        win[t[order][first]] = order[first]
+        assert np.array_equal(x["winner"][p].reshape(-1), win)
+        for tt in range(N * N):
+            j, i = divmod(tt, N)
+            k = win[tt]
+            if k < 0:
+                assert d[p, j, i] == -1.0
+                continue
+            assert k < 300
+            assert d[p, j, i] == np.float32(np.sqrt(q[k])) and np.array_equal(r[p, j, i], rgb[k])
+            np.testing.assert_allclose(n[p, j, i], -(pts[k] - O) / np.sqrt(q[k]), atol=1e-7)
+        # the duplicates tie exactly with their originals: undecided for a float32 builder
+        dup = np.nonzero((win >= 0) & (win < 40))[0]  # texels won by a point that has a duplicate
+        assert len(dup) > 0 and not np.any(x["decided"][p].reshape(-1)[dup])
+
+
+def _float32_recipe(pts, O, N):
+    """The float32 binning and ranking the GPU builder documents in its C ABI
+    (a reimplementation of that recipe, not of the oracle): correctly rounded
+    float32 operations in the stated order. Returns texel, |v|^2 (float32)."""
+    f = np.float32
+    v = pts.astype(f) - O.astype(f)
+    q = (v[:, 0] * v[:, 0] + v[:, 1] * v[:, 1]) + v[:, 2] * v[:, 2]
+    s = (np.abs(v[:, 0]) + np.abs(v[:, 1])) + np.abs(v[:, 2])
+    inv = f(1) / s
+    px, py = v[:, 0] * inv, v[:, 1] * inv
+    lower = v[:, 2] < 0
+    sx = np.where(px >= 0, f(1), f(-1))
+    sy = np.where(py >= 0, f(1), f(-1))
+    fx, fy = (f(1) - np.abs(py)) * sx, (f(1) - np.abs(px)) * sy
+    px, py = np.where(lower, fx, px), np.where(lower, fy, py)
+    half = f(N // 2)
+    i = np.clip(np.floor((px + f(1)) * half).astype(np.int64), 0, N - 1)
+    j = np.clip(np.floor((py + f(1)) * half).astype(np.int64), 0, N - 1)
+    return i + N * j, q
+
+
+def _near_boundary_cloud(rng, O, N, n):
+    """Points whose octahedral coordinate sits within a few float32 ulps of a
+    texel boundary (where float32 and double can bin differently), with
+    distances spread so that winners are contested."""
+    b = rng.integers(1, N, (n, 2)) * (2.0 / N) - 1.0  # boundary lines x, y
+    p = rng.uniform(-1, 1, (n, 2))
+    on_x = rng.uniform(size=n) < 0.5
+    p[on_x, 0] = b[on_x, 0] + rng.normal(scale=4e-7, size=on_x.sum())
+    p[~on_x, 1] = b[~on_x, 1] + rng.normal(scale=4e-7, size=(~on_x).sum())
+    p = np.clip(p, -1, 1)
+    d = oracle.oct_decode(p)
+    r = rng.uniform(0.5, 0.5005, n)  # near-equal distances: contested winners
+    return (O[None] + d * r[:, None]).astype(np.float32)
+
+
+@pytest.mark.parametrize("N", [16, 64, 96])
+def test_decided_texels_are_identical_under_float32_rounding(N):
+    """The 'decided' flag is sound: on an adversarial cloud (points within a
+    few float32 ulps of texel boundaries and near-equal distances), the
+    float32 recipe's winner equals the double-precision winner on every
+    decided texel, while some undecided texels do get another winner (the
+    flag is needed), and the float32 winner is never nearer than dcand."""
+    rng = np.random.default_rng(N)
+    O = np.float32([0.1, -0.2, 0.3])
+    far = rng.normal(size=(20000, 3))
+    far *= rng.uniform(0.6, 2.0, (len(far), 1)) / np.linalg.norm(far, axis=1, keepdims=True)
+    pts = np.concatenate([_near_boundary_cloud(rng, O, N, 12 * N), (O + far).astype(np.float32)])
+    d, n, r, x = oracle.splat_probes(pts, pts, O[None], N, details=True)
+    t32, q32 = _float32_recipe(pts, O, N)
+    order = np.lexsort((np.arange(len(pts)), q32, t32))
+    first = np.ones(len(order), bool)
+    first[1:] = t32[order][1:] != t32[order][:-1]
+    win32 = np.full(N * N, -1)
+    win32[t32[order][first]] = order[first]
+    win64 = x["winner"][0].reshape(-1)
+    dec = x["decided"][0].reshape(-1)
+    assert np.array_equal(win32[dec], win64[dec])
+    assert np.any(win32[~dec] != win64[~dec])
+    assert 0.2 < dec.mean() < 1.0  # a real share of texels stays checkable
+    filled = win32 >= 0
+    d32 = np.sqrt(q32[win32[filled]].astype(np.float64))
+    assert np.all(d32 >= x["dcand"][0].reshape(-1)[filled].astype(np.float64) * (1 - 1e-6))
+
+
+def test_points_on_a_texel_boundary_leave_both_sides_undecided():
+    """A single point exactly on the boundary between texels (3, 2) and
+    (4, 2) of an N = 8 map: either side is a valid float32 outcome, so both
+    are undecided; every other texel is empty and decided."""
+    N = 8
+    O = np.zeros(3, np.float32)
+    pdir = oracle.oct_decode(np.array([[0.0, 2 * 2.5 / N - 1]]))
+    pt = (0.5 * pdir).astype(np.float32)
+    e = oracle.oct_encode(pt.astype(np.float64))[0]
+    assert abs(e[0]) < 1e-7  # on the boundary u = 1/2, i.e. between columns 3 and 4
+    d, n, r, x = oracle.splat_probes(pt, pt, O[None], N, empty_dist=-1.0, details=True)
+    j = int(np.floor((e[1] + 1) / 2 * N))
+    dec = x["decided"][0]
+    assert not dec[j, 3] and not dec[j, 4]
+    assert dec.sum() == N * N - 2
 
 
 @pytest.fixture(scope="module")
