@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--views", type=int, default=64, help="multiscale: number of views (64 in the configuration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="room: leave out the batched FP16 form the default line carries as 'batched'")
     ap.add_argument("--occupancy", default="auto", choices=["auto", "8", "9"],
                     help="batched / multiscale: the autotuner's launch configuration (default), or the streaming "
                          "engine pinned to 8 blocks per SM (64 registers) or 9 (56 registers); the pinned forms "
@@ -228,20 +230,16 @@ def bytes_model(c, rad_fmt_f16, nrm_fmt_f16):
     return 8 * c["coarse"] + 4 * c["fine"] + s_n * c["normal"] + s_r * c["radiance"] + 13 * c["rays"]
 
 
-def run_lfp(args):
+def measure(args, workload, rank, world, local, with_cpu=True):
+    """One workload's bench line (a dict; printed by the caller)."""
     import torch
     import paper_2507_14624_gb300 as lfpk
     from paper_2507_14624_gb300 import lfp
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    sc, views, d, n, r = build_workload(args.workload)
-    f16 = args.workload == "batched"
+    sc, views, d, n, r = build_workload(workload)
+    f16 = workload == "batched"
     fmt = lfpk.LFP_TEXEL_F16 if f16 else lfpk.LFP_TEXEL_F32
-    trav = lfp.LFP_TRAVERSAL_NEAREST if args.workload == "few" else lfp.LFP_TRAVERSAL_GRID
+    trav = lfp.LFP_TRAVERSAL_NEAREST if workload == "few" else lfp.LFP_TRAVERSAL_GRID
     grid = lfpk.ProbeGrid(sc.grid, radiance_fmt=fmt, normal_fmt=fmt, traversal=trav)
     grid.upload(d, n, r)
     sched = lfpk.LFP_SCHED_PERSISTENT if len(views) > 1 else 0
@@ -330,44 +328,76 @@ def run_lfp(args):
     e2e_t = time.perf_counter() - t0
     e2e_value, _, _ = aggregate_over_ranks(e2e_t, total * e2e_steps, device=dev)
     e2e = {"value": round(e2e_value, 3), "unit": "Mrays/s",
-           "h2d_bytes_per_step": int(nv * 72), "d2h_bytes_per_step": int(total * 13)}
+           "h2d_bytes_per_step": int(nv * 72), "d2h_bytes_per_step": int(total * 13),
+           "form": f"frame loop: {e2e_steps} consecutive frames through lfp_render_to_host_async, each frame's "
+                   "copy and launch tail overlapping the next frame's render; the rate of the whole loop, not "
+                   "the latency of one frame"}
+    del rgb_h, cls_h
 
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (ms_launch / 1e3) / 1e9
-    traffic = ncu_traffic(args.workload, occ_key)
+    traffic = ncu_traffic(workload, occ_key)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": kernel_of(args.workload),
+                "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": kernel_of(workload),
                 "counters_per_launch": counters,
-                "issue": issue_roofline(args.workload, ms_launch, clk.get("sm_mhz"),
+                "issue": issue_roofline(workload, ms_launch, clk.get("sm_mhz"),
                                         torch.cuda.get_device_properties(dev).multi_processor_count, occ_key)}
 
     extra = {}
     if not args.no_adjoint and rank == 0:
         if len(views) > 1:  # the batched views themselves (FP16 texels, FP32 gradient)
-            extra["fwd_adj_ms_per_view"] = fwd_adjoint_on_views(torch, grid, views, dev)
-            extra["fwd_adj_workload"] = f"{args.workload}: its {len(views)} views, forward with aux + adjoint"
+            fa = fwd_adjoint(torch, lfp, grid, views, dev, f16, peak, workload,
+                             f"{workload}: its {len(views)} views, forward with saved state + adjoint")
         else:
-            extra["fwd_adj_ms_per_view"] = fwd_adjoint_ms_per_view(torch, lfpk, dev)
-            extra["fwd_adj_workload"] = "fit: room grid seed 4, 64 views 800x800, forward with aux + adjoint"
+            fa = fwd_adjoint_fit(torch, lfpk, lfp, dev, peak)
+        extra["fwd_adj_ms_per_view"] = fa["ms_per_view"]
+        extra["fwd_adj_workload"] = fa["workload"]
+        extra["fwd_adj"] = fa
     if f16 and rank == 0:
         extra["vs_single_view_fp32"] = single_view_fp32(torch, lfpk, lfp, sc, views, d, n, r, cls, flush,
                                                         value, args.steps)
     cpu = None
-    if not args.no_cpu_baseline and rank == 0 and world == 1:
+    if with_cpu and not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(sc, views, d, n, r, budget_s=10.0, traversal=int(trav))
-    if rank == 0:
-        line = {"metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_launch, 4),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f16+f32" if f16 else "f32", "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
-                "config": workload_info(args.workload, views, sc.grid), "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "cuda_graph": graph is not None,
-                "autotuned": tuned, "occupancy": args.occupancy if args.occupancy != "auto" else occ_key,
-                "roofline": roofline, "clocks": clk,
-                "cpu_baseline": cpu, **extra}
-        print(json.dumps(line), flush=True)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_launch, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16+f32" if f16 else "f32", "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
+            "config": workload_info(workload, views, sc.grid), "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "cuda_graph": graph is not None,
+            "autotuned": tuned, "occupancy": args.occupancy if args.occupancy != "auto" else occ_key,
+            "roofline": roofline, "clocks": clk,
+            "cpu_baseline": cpu, **extra}
+    del graph, flush, rgb, cls
     grid.close()
+    torch.cuda.empty_cache()
+    return line
+
+
+def batched_summary(b):
+    """The keys of the batched FP16 line carried in the default line: the
+    spec comparison of the batched FP16 form with the plain FP32
+    single-view form on the same views, and its forward + adjoint."""
+    keep = ("value", "unit", "ms_per_step", "dtype", "config", "e2e", "gpu_launches", "cuda_graph", "autotuned",
+            "occupancy", "roofline", "clocks", "vs_single_view_fp32", "fwd_adj_ms_per_view", "fwd_adj")
+    return {k: b[k] for k in keep if k in b}
+
+
+def run_lfp(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    line = measure(args, args.workload, rank, world, local)
+    if args.workload == "room" and not args.no_batched and world == 1:
+        # the batched FP16 form on the same GPU in the same run (one GPU only:
+        # under torchrun the timed work per N stays at the room frame)
+        line["batched"] = batched_summary(measure(args, "batched", rank, world, local, with_cpu=False))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -418,56 +448,98 @@ def single_view_fp32(torch, lfpk, lfp, sc, views, d, n, r, cls_f16, flush, batch
             "class_agreement_fp16_vs_fp32": round(agree, 7)}
 
 
-def fwd_adjoint_ms_per_view(torch, lfpk, dev, steps=5):
+# Adjoint bytes per HIT pixel: 12 B of rgb gradient read, 16 B of saved
+# state (probe index, uv, class), 4 bilinear taps x 3 channels x 8 B of
+# read-modify-write into the radiance gradient.
+BWD_BYTES_PER_HIT = 12 + 16 + 4 * 3 * 8
+
+
+def backward_source_sha():
+    h = hashlib.sha256()
+    for f in ("support.cu", "lfp_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2507_14624_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def backward_traffic(workload):
+    """DRAM bytes per adjoint launch from the committed ncu summary (taken on
+    the current adjoint source), or None."""
+    p = os.path.join(ROOT, "profiles", f"backward_{workload}_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("source_sha") == backward_source_sha():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def fwd_adjoint(torch, lfp, grid, views, dev, f16, peak, workload, desc, steps=3, **render_kw):
+    """Forward with saved state + adjoint into an FP32 radiance gradient over
+    the given views on the given grid; times both together and the adjoint
+    alone (CUDA events), and sets them against the algorithmic bytes: the
+    forward's (fetch counters of the counting variant, plus 12 B of saved
+    state per ray) and the adjoint's BWD_BYTES_PER_HIT per HIT pixel."""
+    out = grid.render(views, aux=True, counters=True, **render_kw)
+    counters = dict(zip(lfp.COUNTER_NAMES, (int(x) for x in out["counters"].cpu().tolist())))
+    fwd_b = bytes_model(counters, f16, f16) + 12 * counters["rays"]
+    bwd_b = BWD_BYTES_PER_HIT * counters["hits"]
+    grad_rgb = torch.randn_like(out["rgb"])
+    grad = torch.zeros((grid.n_probes, grid.N, grid.N, 3), dtype=torch.float32, device=dev)
+    del out
+    for _ in range(2):
+        out = grid.render(views, aux=True, **render_kw)
+        grid.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
+        del out
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        out = grid.render(views, aux=True, **render_kw)
+        grid.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
+        del out
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fa = e0.elapsed_time(e1) / steps
+    out = grid.render(views, aux=True, **render_kw)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        grid.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / steps
+    del out, grad, grad_rgb
+    nv = len(views)
+    ach = (fwd_b + bwd_b) / (ms_fa / 1e3) / 1e9
+    ach_b = bwd_b / (ms_b / 1e3) / 1e9
+    return {"ms_per_view": round(ms_fa / nv, 4), "workload": desc, "views": nv, "rays": counters["rays"],
+            "hits": counters["hits"], "bytes_per_step": int(fwd_b + bwd_b), "achieved_gbs": round(ach, 1),
+            "peak_gbs": peak, "frac": round(ach / peak, 4),
+            "backward": {"kernel": "backward_warp_kernel", "ms_per_step": round(ms_b, 4),
+                         "launches_per_step": (nv + 127) // 128, "bytes_per_step": int(bwd_b),
+                         "achieved_gbs": round(ach_b, 1), "frac": round(ach_b / peak, 4),
+                         "traffic_per_launch": backward_traffic(workload),
+                         "bytes_model": "12 B rgb gradient + 16 B saved state + 4 taps x 3 channels x 8 B "
+                                        "read-modify-write per HIT pixel"}}
+
+
+def fwd_adjoint_fit(torch, lfpk, lfp, dev, peak, steps=5):
     """Differentiable-fit workload: the room grid (seed 4), 64 views of
     800x800; one step = batched forward with saved state + adjoint scatter
-    into radiance gradients. Reported per view."""
+    into radiance gradients."""
     import synth
     sc, views = synth.workload("fit")
     d, n, r = sc.probe_maps()
     g = lfpk.ProbeGrid(sc.grid)
     g.upload(d, n, r)
-    out = g.render(views, aux=True, schedule=lfpk.LFP_SCHED_PERSISTENT)
-    grad_rgb = torch.randn_like(out["rgb"])
-    grad = torch.zeros((g.n_probes, g.N, g.N, 3), dtype=torch.float32, device=dev)
-    for _ in range(2):
-        out = g.render(views, aux=True, schedule=lfpk.LFP_SCHED_PERSISTENT)
-        g.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        out = g.render(views, aux=True, schedule=lfpk.LFP_SCHED_PERSISTENT)
-        g.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
-    e1.record()
-    torch.cuda.synchronize()
+    res = fwd_adjoint(torch, lfp, g, views, dev, False, peak, "fit",
+                      "fit: room grid seed 4, 64 views 800x800, forward with saved state + adjoint", steps=steps,
+                      schedule=lfpk.LFP_SCHED_PERSISTENT)
     g.close()
-    return round(e0.elapsed_time(e1) / steps / len(views), 4)
-
-
-def fwd_adjoint_on_views(torch, grid, views, dev, steps=3):
-    """Forward with saved state + adjoint into an FP32 radiance gradient over
-    the given views on the given grid (its launch configuration as tuned);
-    ms per view."""
-    out = grid.render(views, aux=True)
-    grad_rgb = torch.randn_like(out["rgb"])
-    grad = torch.zeros((grid.n_probes, grid.N, grid.N, 3), dtype=torch.float32, device=dev)
-    del out
-    for _ in range(2):
-        out = grid.render(views, aux=True)
-        grid.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
-        del out
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        out = grid.render(views, aux=True)
-        grid.render_backward(views, grad_rgb, out["cls"], out["probe"], out["uv"], grad)
-        del out
-    e1.record()
-    torch.cuda.synchronize()
-    del grad, grad_rgb
-    return round(e0.elapsed_time(e1) / steps / len(views), 4)
+    return res
 
 
 def cpu_baseline(sc, views, d, n, r, budget_s=10.0, max_reps=10, traversal=0):

@@ -30,6 +30,15 @@
  *     failure is reported as LFP_ERR_CUDA (checked with cudaGetLastError).
  *   - The library is not thread-safe per grid: calls on one grid must come
  *     from one host thread at a time. Distinct grids are independent.
+ *   - Renders of one grid share its work-queue head (a device counter that
+ *     every launch resets and then consumes): lfp_render, lfp_render_ex,
+ *     lfp_render_to_host, lfp_autotune and lfp_render_levels. Such calls
+ *     must run one after another on the GPU: issue them on one stream, and
+ *     do not replay a CUDA graph that recorded one of them while another
+ *     render of the same grid may run. Two that overlap corrupt each other's
+ *     queue (rays skipped or rendered twice). lfp_render_to_host_async uses
+ *     two queue heads of its own and lfp_render_static one per process (see
+ *     there); the adjoint and the probe builder use none.
  */
 #ifndef LFP_H
 #define LFP_H
@@ -284,25 +293,29 @@ lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes);
 /* Most views one lfp_render_static call accepts. */
 #define LFP_STATIC_MAX_VIEWS 4096
 
-/* Forward render that allocates nothing (the paper has no counterpart: this
- * is an interface for callers that cannot allocate device memory at render
- * time -- a render recorded during CUDA stream capture, where cudaMalloc is
- * not allowed; a real-time frame loop that must not touch the allocator after
- * start-up; a host whose device memory comes from its own fixed-budget
- * allocator). Same results and outputs as lfp_render_ex with
+/* Forward render that allocates nothing (the paper has no counterpart). It
+ * is for callers that cannot allocate device memory at render time: a
+ * real-time frame loop that must not touch the allocator after start-up
+ * (cudaMalloc and cudaFree can synchronise the whole device and stall the
+ * loop), or a host application or plug-in whose device memory comes from its
+ * own fixed-budget allocator, which a library allocating behind its back
+ * would break. Same results and outputs as lfp_render_ex with
  * LFP_ENGINE_NESTED, LFP_SCHED_PERSISTENT and 16x8 ray tiles, in one
- * persistent launch for all
- * n_views <= LFP_STATIC_MAX_VIEWS views (more -> LFP_ERR_CAPACITY, nothing
- * is launched). The work-queue head and the view table live in one
- * file-scope device array of 256 B + LFP_STATIC_MAX_VIEWS * 80 B (about
- * 320 KiB) that every GPU loading the library keeps until the process exits.
+ * persistent launch for all n_views <= LFP_STATIC_MAX_VIEWS views (more ->
+ * LFP_ERR_CAPACITY, nothing is launched). The work-queue head and the view
+ * table live in one file-scope device array of 256 B + LFP_STATIC_MAX_VIEWS
+ * * 80 B (about 320 KiB) that every GPU loading the library keeps until the
+ * process exits. The call issues small fill kernels that carry the view
+ * entries in their parameters, a 4-byte memset of the queue head, and the
+ * render; it calls no cudaMalloc, cudaFree or other allocating routine.
  *   - The first call on a device sets that device up (looks up the array's
- *     device address, sizes the persistent grid); make that first call
- *     before any stream capture.
- *   - All calls share the array: the queue head is cleared by every call and
- *     the view table is rewritten, so calls that overlap on the GPU (other
- *     streams, other host threads) race; serialise them on one stream.
- *   - `views` is host memory, copied before the call returns.
+ *     device address with cudaGetSymbolAddress, sizes the persistent grid);
+ *     make that first call before any stream capture.
+ *   - All calls share the array: every call rewrites the view table and
+ *     clears the queue head, so calls that overlap on the GPU (other streams,
+ *     other host threads' streams) race; serialise them on one stream.
+ *   - `views` is host memory, read before the call returns (the call does
+ *     not wait for the stream).
  *   - grid: created and uploaded beforehand (those calls do allocate). */
 lfp_status lfp_render_static(lfp_grid* grid, const lfp_view* views, int n_views,
                              const lfp_outputs* out, void* cuda_stream);

@@ -1,16 +1,20 @@
 // lfp_render_static: a forward render that allocates nothing.
 //
-// Some callers cannot call cudaMalloc at render time: code that records the
-// render while a CUDA stream is being captured into a graph (allocation is not
-// a capturable operation), real-time frame loops that must not touch the
-// allocator after start-up, and hosts whose device memory is handed out by
-// their own fixed-budget allocator. lfp_render_ex itself does not allocate,
-// but its persistent schedule keeps its work-queue head in memory the grid
-// allocated, and it splits large batches into several launches because views
-// travel as kernel parameters. This entry point instead keeps the queue head
-// and the view table in one file-scope __device__ array of fixed size, so one
-// persistent launch covers up to LFP_STATIC_MAX_VIEWS views and the call
-// performs no allocation of any kind.
+// Some callers cannot allocate device memory while they render: a real-time
+// frame loop that must not touch the allocator after start-up (cudaMalloc
+// and cudaFree can synchronise the device and stall the loop), or a host
+// application or plug-in whose device memory is handed out by its own
+// fixed-budget allocator, so that a library allocating behind its back would
+// break the budget. lfp_render_ex itself does not allocate, but its
+// persistent schedule keeps its work-queue head in memory the grid
+// allocated, and it splits large batches into several launches because
+// views travel as kernel parameters. This entry point instead keeps the
+// queue head and the view table in one file-scope __device__ array of fixed
+// size, so one persistent launch covers up to LFP_STATIC_MAX_VIEWS views and
+// the call performs no allocation of any kind. The view table is written by
+// small fill kernels that carry the entries in their parameters, so the
+// call reads no host memory after it returns and does not wait for the
+// stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,12 +33,26 @@ using namespace trace;
 constexpr int kTileW = 16, kTileH = 8;
 constexpr size_t kHeadBytes = 256;  // queue head (word 0), rest unused
 constexpr size_t kScratchBytes = kHeadBytes + (size_t)LFP_STATIC_MAX_VIEWS * sizeof(ViewDev);
+// views per fill launch: 48 x 80 B of entries keep the parameter block
+// under the classic 4 KB kernel-parameter limit
+constexpr int kFillViews = 48;
 
 // The scratch every call shares: queue head at offset 0, the view table at
 // kHeadBytes. Each GPU that loads the library holds its own copy until the
 // process exits. In host code this name is only a stand-in for the device
 // address; host code uses the address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_render_scratch[kScratchBytes];
+
+// A chunk of the view table, passed by value as a kernel parameter.
+struct TableChunk {
+    int first, n;
+    ViewDev v[kFillViews];
+};
+static_assert(sizeof(TableChunk) + sizeof(void*) <= 4000, "fill kernel parameters must stay under 4 KB");
+
+__global__ void fill_table_kernel(const __grid_constant__ TableChunk c, ViewDev* table) {
+    if ((int)threadIdx.x < c.n) table[c.first + threadIdx.x] = c.v[threadIdx.x];
+}
 
 template <int RADF, int NRMF, bool COUNT>
 __global__ void __launch_bounds__(256) render_table_kernel(GridDev g, const ViewDev* __restrict__ views, int n_views,
@@ -128,8 +146,7 @@ struct DeviceSetup {
     int blocks[2][2][2] = {};  // [rad_fmt][nrm_fmt][count]
 };
 DeviceSetup g_setup[kMaxDevices];
-ViewDev g_host_table[LFP_STATIC_MAX_VIEWS];  // host staging, static storage
-std::mutex g_mutex;                          // guards g_setup and g_host_table
+std::mutex g_mutex;  // guards g_setup; keeps one call's launches together on a stream
 
 lfp_status setup_device(int device, int sm_count, DeviceSetup** out) {
     if (device < 0 || device >= kMaxDevices) return LFP_ERR_CUDA;
@@ -182,13 +199,23 @@ extern "C" lfp_status lfp_render_static(lfp_grid* grid, const lfp_view* views, i
         DeviceSetup* ds = nullptr;
         st = setup_device(ga.device, ga.sm_count, &ds);
         if (st == LFP_OK) {
-            long long t = 0;
-            for (int i = 0; i < n_views; ++i) {
-                g_host_table[i] = view_dev_of(views[i], kTileW, kTileH, (int)t);
-                t += (long long)g_host_table[i].tiles_x * ((views[i].H + kTileH - 1) / kTileH);
-            }
             unsigned* queue = reinterpret_cast<unsigned*>(ds->scratch);
             ViewDev* table = reinterpret_cast<ViewDev*>(ds->scratch + kHeadBytes);
+            // the view table, kFillViews entries per fill launch (the entries
+            // travel in the launch's parameters)
+            TableChunk chunk;
+            long long t = 0;
+            for (int first = 0; first < n_views && st == LFP_OK; first += kFillViews) {
+                chunk.first = first;
+                chunk.n = std::min(kFillViews, n_views - first);
+                for (int i = 0; i < chunk.n; ++i) {
+                    const lfp_view& v = views[first + i];
+                    chunk.v[i] = view_dev_of(v, kTileW, kTileH, (int)t);
+                    t += (long long)chunk.v[i].tiles_x * ((v.H + kTileH - 1) / kTileH);
+                }
+                fill_table_kernel<<<1, kFillViews, 0, s>>>(chunk, table);
+                if (cudaGetLastError() != cudaSuccess) st = LFP_ERR_CUDA;
+            }
             OutDev out;
             out.rgb = o->rgb;
             out.cls = o->cls;
@@ -197,13 +224,8 @@ extern "C" lfp_status lfp_render_static(lfp_grid* grid, const lfp_view* views, i
             out.hit_texel = o->hit_texel;
             out.counters = o->counters;
             bool count = o->counters != nullptr;
-            // pageable source: the call returns once the table has been staged,
-            // so g_host_table may be rewritten by the next call
-            if (cudaMemcpyAsync(table, g_host_table, sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, s) !=
-                    cudaSuccess ||
-                cudaMemsetAsync(queue, 0, sizeof(unsigned), s) != cudaSuccess) {
-                st = LFP_ERR_CUDA;
-            } else {
+            if (st == LFP_OK && cudaMemsetAsync(queue, 0, sizeof(unsigned), s) != cudaSuccess) st = LFP_ERR_CUDA;
+            if (st == LFP_OK) {
                 int blocks = ds->blocks[ga.rad_fmt][ga.nrm_fmt][count ? 1 : 0];
                 pick_kernel(ga.rad_fmt, ga.nrm_fmt, count)<<<blocks, kTileW * kTileH, 0, s>>>(
                     ga.dev, table, n_views, (int)tiles, out, queue);

@@ -113,3 +113,17 @@ def test_autotune_cache_key_and_file(tmp_path):
     got = lfpk._read_tune_cache(path)
     assert got[k1] == {"engine": 2, "tile": [16, 8], "schedule": 2, "occupancy": 0}
     assert got["other"]["engine"] == 1
+
+
+def test_adjoint_bytes_and_traffic_summary(tmp_path, monkeypatch):
+    # 12 B gradient + 16 B saved state + 4 taps x 3 channels x 8 B read-modify-write
+    assert bench.BWD_BYTES_PER_HIT == 124
+    (tmp_path / "profiles").mkdir()
+    p = tmp_path / "profiles" / "backward_fit_traffic.json"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "backward_source_sha", lambda: "cur")
+    p.write_text(json.dumps({"source_sha": "cur", "dram_bytes_per_launch": 123.0}))
+    assert bench.backward_traffic("fit") == 123.0
+    p.write_text(json.dumps({"source_sha": "old", "dram_bytes_per_launch": 123.0}))
+    assert bench.backward_traffic("fit") is None  # taken on another adjoint source
+    assert bench.backward_traffic("batched") is None  # no summary

@@ -1,9 +1,11 @@
 """Seeded randomized parity: many small grids and views against the FP64
 oracle, through the default (streaming) engine, with the agreement rule of
 test_gpu_parity. Each case draws the grid shape (2..4 per axis), spacing,
-origin, map sides (N with N / M in {2, 4, 8, 16}), thickness rule, texel
-formats, scene density and camera (inside or outside the cage, any FOV in
-40..110 degrees, odd and even image sizes)."""
+origin, map sides, thickness rule, texel formats, scene density and camera
+(inside or outside the cage, any FOV in 40..110 degrees, odd and even image
+sizes). The first set draws powers of two (N in {16..128}, N / M in {2, 4,
+8, 16}); the second non-powers of two (N in {48, 96, 192}, block side
+k = N / M in {3, 6, 12})."""
 import numpy as np
 import pytest
 
@@ -15,14 +17,18 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _case(seed):
+def _case(seed, pow2=True):
     rng = np.random.default_rng(seed)
     dims = tuple(int(x) for x in rng.integers(2, 5, 3))
     spacing = float(rng.choice([0.25, 0.5, 1.0, 1.5]))
     origin = tuple(float(np.float32(x)) for x in rng.uniform(-2, 2, 3))
-    N = int(rng.choice([16, 32, 64, 128]))
-    M = N // int(rng.choice([2, 4, 8, 16]))
-    M = max(2, M - (M % 2))
+    if pow2:
+        N = int(rng.choice([16, 32, 64, 128]))
+        M = N // int(rng.choice([2, 4, 8, 16]))
+        M = max(2, M - (M % 2))
+    else:  # M = N / k stays even for every pair drawn here
+        N = int(rng.choice([48, 96, 192]))
+        M = N // int(rng.choice([3, 6, 12]))
     th = float(rng.choice([1.0, 1.0, 0.5, 2.0, -1.0]))
     f16 = bool(rng.random() < 0.3)
     g = synth.Grid(*dims, spacing, N, M, origin)
@@ -41,10 +47,11 @@ def _case(seed):
     return g, sc, v, th, f16
 
 
-@pytest.mark.parametrize("seed", list(range(1000, 1024)))
-def test_random_configuration_matches_oracle(seed):
+@pytest.mark.parametrize("seed,pow2", [(s, True) for s in range(1000, 1024)] +
+                         [(s, False) for s in range(2000, 2016)])
+def test_random_configuration_matches_oracle(seed, pow2):
     import paper_2507_14624_gb300 as lfpk
-    g, sc, v, th, f16 = _case(seed)
+    g, sc, v, th, f16 = _case(seed, pow2)
     d, n, r = sc.probe_maps()
     fmt = lfpk.LFP_TEXEL_F16 if f16 else lfpk.LFP_TEXEL_F32
     grid = lfpk.ProbeGrid(g, radiance_fmt=fmt, normal_fmt=fmt, thickness_rel=th)

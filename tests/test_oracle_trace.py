@@ -296,3 +296,21 @@ def test_hit_point_is_the_analytic_root(case):
         if case != "behind_receding":  # the point found lies on the ray at the expected radius
             rad = np.linalg.norm(Y0 + th * w)
             assert abs(rad - (R if case != "never_reaches" else np.sqrt(np.dot(Y0, Y0) - B * B))) <= 1e-9
+
+
+@pytest.mark.parametrize("N,M", [(48, 16), (96, 8), (192, 16), (192, 8), (144, 6), (192, 4)])
+def test_hierarchical_march_equals_flat_march_at_odd_block_sizes(N, M):
+    """The min/max skip is exact for any block side k = N / M, including the
+    non-powers of two of the resolution study (k = 3, 12, 24, 48 here): class,
+    probe, hit texel and radiance agree with the flat march on every pixel."""
+    g = synth.Grid(3, 3, 2, 0.5, N, M)
+    sc = synth.make_scene(g, 12, 4, [0.7, 0.3], seed=N + M)
+    v = synth.random_view(sc, 300 + N, 64, 48, 70.0)
+    d, n, r = sc.probe_maps()
+    o = oracle.Oracle(g, d, n, r)
+    flat = o.render(v, march=oracle.MARCH_FLAT)
+    for mode in (oracle.MARCH_HIER, oracle.MARCH_HIER_SHORTCUT):
+        h = o.render(v, march=mode)
+        for k in ("cls", "probe", "texel", "rgb"):
+            assert np.array_equal(h[k], flat[k]), (N, M, k)
+    assert (flat["cls"] == oracle.HIT).mean() > 0.8

@@ -1,13 +1,13 @@
 """lfp_render_static: the forward render that allocates nothing.
 
-It exists for callers that cannot allocate device memory while they render
-(a render recorded into a CUDA graph during stream capture, a frame loop that
-must not touch the allocator after start-up, a host with its own fixed device
-budget). It keeps its work-queue head and view table in a fixed file-scope
-device array, so this test checks, through the C ABI, that two calls in a row
-(the second with different views, so the shared array is reused) give the
-same images as lfp_render_ex with the persistent schedule, and that a request
-beyond the array's capacity is refused before anything runs.
+It exists for callers that cannot allocate device memory while they render:
+a real-time frame loop that must not touch the allocator after start-up, or a
+host whose device memory comes from its own fixed-budget allocator. It keeps
+its work-queue head and view table in a fixed file-scope device array, so this
+test checks, through the C ABI, that two calls in a row (the second with
+different views, so the shared array is reused) give the same images as
+lfp_render_ex with the persistent schedule, and that a request beyond the
+array's capacity is refused before anything runs.
 """
 import ctypes
 
