@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--views", type=int, default=64, help="multiscale: number of views (64 in the configuration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--log-every", type=int, default=0,
+                    help="fit: record the MSE every this many iterations (synchronises; for convergence runs)")
     ap.add_argument("--no-batched", action="store_true",
                     help="room: leave out the batched FP16 form the default line carries as 'batched'")
     ap.add_argument("--occupancy", default="auto", choices=["auto", "8", "9"],
@@ -1120,6 +1122,18 @@ def run_complexity(args):
     print(json.dumps(line), flush=True)
 
 
+def convergence(hist, floor, log_every):
+    """First logged iteration whose MSE is within 2x, 1.5x and 1.1x of the
+    noise floor, and the logged trajectory (only when logging was asked for:
+    the per-step read-back synchronises, so such a run is not a timing run)."""
+    if not log_every:
+        return {}
+    out = {"mse_history": [[int(s), float(m)] for s, m, _ in hist]}
+    for f in (2.0, 1.5, 1.1):
+        out[f"first_step_within_{f}x_floor"] = next((int(s) for s, m, _ in hist if m <= f * floor), None)
+    return out
+
+
 def run_fit(args):
     """Differentiable fit: the room grid (seed 4), 64 views of 800x800, targets
     = ground-truth render + N(0, 0.01^2); radiance re-initialised U[0,1]; L2
@@ -1142,7 +1156,8 @@ def run_fit(args):
     total = sum(v.W * v.H for v in views)
     targets = fit.make_targets(g, mine, sigma=0.01, seed=404 + rank)
     fit.fit_radiance(g, mine, targets, steps=args.warmup, lr=1e-2, seed=404, total_pixels=total)
-    rad, hist = fit.fit_radiance(g, mine, targets, steps=args.steps, lr=1e-2, seed=404, total_pixels=total)
+    rad, hist = fit.fit_radiance(g, mine, targets, steps=args.steps, lr=1e-2, seed=404, total_pixels=total,
+                                 log_every=args.log_every)
     ms = hist[-1][2]
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -1153,6 +1168,7 @@ def run_fit(args):
                 "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "scaling": "strong", "ms_per_view": round(ms / len(views), 4),
                 "final_mse": hist[-1][1], "noise_floor": 1e-4, "dtype": "f32",
+                **convergence(hist, 1e-4, args.log_every),
                 "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
                 "config": {"workload": "fit: room grid seed 4, 64 views 800x800, sigma 0.01, Adam lr 1e-2",
                            "parallelism": f"dp{world}: views split over ranks, radiance gradient all-reduced"}}

@@ -79,10 +79,23 @@ enum ColdF {
 };
 enum ColdI { kC0, kC1, kC2, kCbits, kOrder, kQ, kKq, kSegI, kSegFinal, kCls, kQuad, kI, kJ, kLastc, kNumColdI };
 // kCbits: step signs (2 bits per axis: 1 +, 2 -), bits 6-7 exit axis, bit 8
-// last cell, bit 9 saw UNKNOWN. kOrder: corner of rank q in bits [3q, 3q + 3).
+// last cell, bit 9 saw UNKNOWN, bit 10 the cage order of the current cell
+// is already in kOrder (first cell of a ray from inside the grid; cleared by
+// cell_start). kOrder: corner of rank q in bits [3q, 3q + 3).
 __shared__ float sh_f[kNumColdF][kStreamThreads];
 __shared__ int sh_i[kNumColdI][kStreamThreads];
 __shared__ long long sh_o[kStreamThreads];  // output index of the lane's ray
+
+// Per-warp constants of the view the warp's current tile belongs to. Every
+// primary ray of a view starts at the camera X, so the view's index, the
+// eye-aligned test (Sec. 4.2), the grid entry when X lies in the probe box
+// (the cell holding X, from t = 0) and that first cell's cage order (nearest
+// to X), or the nearest-probe order of the traversal for fewer than 8
+// probes, are the same for all of its rays: they are computed once per tile
+// (same operations as per ray, so decisions do not change).
+enum WarpViewF { kWvView, kWvEye, kWvInside, kWvC0, kWvC1, kWvC2, kWvOrder, kWvNum };
+__shared__ int sh_wv[kStreamThreads / 32][kWvNum];
+__device__ __forceinline__ int& WV(int f) { return sh_wv[threadIdx.x >> 5][f]; }
 
 __device__ __forceinline__ float& CF(int f) { return sh_f[f][threadIdx.x]; }
 __device__ __forceinline__ int& CI(int f) { return sh_i[f][threadIdx.x]; }
@@ -156,9 +169,11 @@ __device__ __forceinline__ void cell_start(const GridDev& g) {
     float tax = ax == 0 ? tm[0] : (ax == 1 ? tm[1] : tm[2]);
     CI(kCbits) = (cbits & 0x23f) | (ax << 6) | (last ? 0x100 : 0);
     CF(kTout) = last ? kInf : tax;
-    const float t_in = CF(kTin);
-    float3 P = make_float3(fmaf(t_in, w.x, X.x), fmaf(t_in, w.y, X.y), fmaf(t_in, w.z, X.z));
-    CI(kOrder) = (int)cage_order(g, c[0], c[1], c[2], P);
+    if (!(cbits & 0x400)) {  // else the first cell of a ray from inside the grid: order set from the view
+        const float t_in = CF(kTin);
+        float3 P = make_float3(fmaf(t_in, w.x, X.x), fmaf(t_in, w.y, X.y), fmaf(t_in, w.z, X.z));
+        CI(kOrder) = (int)cage_order(g, c[0], c[1], c[2], P);
+    }
     CI(kQ) = 0;
 }
 
@@ -428,7 +443,7 @@ __device__ __forceinline__ void decide(const GridDev& g, Lane& L, Stats<COUNT>& 
 // Traversal for fewer than 8 probes (Sec. 4.3): every probe, nearest to the
 // eye first (squared distances, ties to the lower index, the same arithmetic
 // as the loop-nest engine), as one pseudo-cell over [0, inf).
-__device__ __forceinline__ void nearest_start(const GridDev& g, float3 X) {
+__device__ __forceinline__ unsigned nearest_order(const GridDev& g, float3 X) {
     const int P = g.nx * g.ny * g.nz;  // <= 8, checked at grid creation
     float d2[8];
 #pragma unroll
@@ -450,6 +465,10 @@ __device__ __forceinline__ void nearest_start(const GridDev& g, float3 X) {
         used |= 1u << pick;
         order |= (unsigned)pick << (3 * q);
     }
+    return order;
+}
+
+__device__ __forceinline__ void nearest_start(unsigned order) {
     CI(kOrder) = (int)order;
     CI(kQ) = 0;
     CI(kCbits) = 0x100;  // the one pseudo-cell is the last
@@ -457,15 +476,57 @@ __device__ __forceinline__ void nearest_start(const GridDev& g, float3 X) {
     CF(kTout) = kInf;
 }
 
-// Start the ray of slot `slot` (0..31) of 8x4 ray tile `tile`.
+// The view constants of tile `tile` into the warp's slots (warp-uniform:
+// every lane computes and writes the same values).
 template <bool NEAREST>
-__device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb, int tile, int slot, Lane& L) {
+__device__ __forceinline__ void warp_view_setup(const GridDev& g, const ViewBatch& vb, int tile) {
     int lo = 0, hi = vb.n - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (vb.v[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
     }
     const ViewDev& v = vb.v[lo];
+    const float3 X = make_float3(v.px, v.py, v.pz);
+    // eye aligned with a probe: the nearest grid vertex within eye_eps
+    const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
+    const float og[3] = {g.ox, g.oy, g.oz}, Xa[3] = {X.x, X.y, X.z};
+    int iv[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) iv[q] = min(max((int)rintf(fdiv(Xa[q] - og[q], g.spacing)), 0), nc[q]);
+    const float3 O = corner_pos(g, iv[0], iv[1], iv[2], 0);
+    const float ex = X.x - O.x, ey = X.y - O.y, ez = X.z - O.z;
+    const bool eye = sqrtf(ex * ex + ey * ey + ez * ez) < g.eye_eps;
+    int inside = 0, c[3] = {0, 0, 0};
+    unsigned order = 0;
+    if (NEAREST) {
+        order = nearest_order(g, X);
+    } else {
+        // a camera in the closed probe box enters the grid at t = 0 for every
+        // direction, in the cell holding it (the arithmetic of ray_enter_grid)
+        inside = 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float lo_a = grid_plane(og[a], g.spacing, 0), hi_a = grid_plane(og[a], g.spacing, nc[a]);
+            if (!(Xa[a] >= lo_a && Xa[a] <= hi_a)) inside = 0;
+            c[a] = min(max((int)floorf(fdiv(Xa[a] - og[a], g.spacing)), 0), nc[a] - 1);
+        }
+        if (inside) order = cage_order(g, c[0], c[1], c[2], X);
+    }
+    WV(kWvView) = lo;
+    WV(kWvEye) = eye ? iv[0] + g.nx * (iv[1] + g.ny * iv[2]) : -1;
+    WV(kWvInside) = inside;
+    WV(kWvC0) = c[0];
+    WV(kWvC1) = c[1];
+    WV(kWvC2) = c[2];
+    WV(kWvOrder) = (int)order;
+    __syncwarp();
+}
+
+// Start the ray of slot `slot` (0..31) of 8x4 ray tile `tile` (whose view
+// constants are in the warp's slots).
+template <bool NEAREST>
+__device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb, int tile, int slot, Lane& L) {
+    const ViewDev& v = vb.v[WV(kWvView)];
     int lt = tile - v.tile_begin;
     int x = (lt % v.tiles_x) * 8 + (slot & 7), y = (lt / v.tiles_x) * 4 + (slot >> 3);
     if (x >= v.W || y >= v.H) {
@@ -486,20 +547,11 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
     CF(kW2) = w.z;
     sh_o[threadIdx.x] = v.out_offset + (long long)y * v.W + x;
     CI(kCls) = kMiss;
-    // eye aligned with a probe (Sec. 4.2): the nearest grid vertex within
-    // eye_eps is looked up at oct(w) directly
-    const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
-    const float og[3] = {g.ox, g.oy, g.oz}, Xa[3] = {X.x, X.y, X.z};
-    int iv[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) iv[q] = min(max((int)rintf(fdiv(Xa[q] - og[q], g.spacing)), 0), nc[q]);
-    int p = iv[0] + g.nx * (iv[1] + g.ny * iv[2]);
-    float3 O = corner_pos(g, iv[0], iv[1], iv[2], 0);
-    float ex = X.x - O.x, ey = X.y - O.y, ez = X.z - O.z;
-    if (sqrtf(ex * ex + ey * ey + ez * ez) < g.eye_eps) {
+    const int eye_probe = WV(kWvEye);
+    if (eye_probe >= 0) {  // eye aligned with a probe (Sec. 4.2): look up oct(w) directly
         float2 pp = oct_encode(w.x, w.y, w.z);
         CI(kCls) = kHit;
-        L.probe = p;
+        L.probe = eye_probe;
         L.ux = 0.5f * (pp.x + 1.0f);
         L.uy = 0.5f * (pp.y + 1.0f);
         L.i = texel_of(pp.x, g.N, 1);
@@ -512,8 +564,19 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
         return;
     }
     if (NEAREST) {
-        nearest_start(g, X);
+        nearest_start((unsigned)WV(kWvOrder));
         L.mode = kProbeStart;
+        return;
+    }
+    if (WV(kWvInside)) {  // the view's first cell and its cage order
+        CI(kC0) = WV(kWvC0);
+        CI(kC1) = WV(kWvC1);
+        CI(kC2) = WV(kWvC2);
+        CI(kCbits) = (w.x > 0.0f ? 1 : (w.x < 0.0f ? 2 : 0)) | (w.y > 0.0f ? 4 : (w.y < 0.0f ? 8 : 0)) |
+                     (w.z > 0.0f ? 16 : (w.z < 0.0f ? 32 : 0)) | 0x400;
+        CI(kOrder) = WV(kWvOrder);
+        CF(kTin) = 0.0f;
+        L.mode = kCellStart;
         return;
     }
     L.mode = ray_enter_grid(g, X, w) ? kCellStart : kRayDone;
@@ -607,6 +670,7 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
                     }
                     pool = ((sub & 1) * 16) | (((sub & 1) * 16 + 16) << 6);
                 }
+                warp_view_setup<NEAREST>(g, vb, pool_tile);
             }
             const int pool_next = pool & 63;
             int avail = (pool >> 6) - pool_next;
