@@ -151,12 +151,20 @@ __device__ __forceinline__ void bilinear_taps(int N, float u, float v, int idx[4
     float fs = floorf(s), ft = floorf(t);
     int i0 = (int)fs, j0 = (int)ft;
     float a = s - fs, b = t - ft;
-    int ci[4] = {i0, i0 + 1, i0, i0 + 1};
-    int cj[4] = {j0, j0, j0 + 1, j0 + 1};
     w[0] = (1.0f - a) * (1.0f - b);
     w[1] = a * (1.0f - b);
     w[2] = (1.0f - a) * b;
     w[3] = a * b;
+    if ((unsigned)i0 < (unsigned)(N - 1) && (unsigned)j0 < (unsigned)(N - 1)) {  // all four taps inside
+        const int base = i0 + N * j0;
+        idx[0] = base;
+        idx[1] = base + 1;
+        idx[2] = base + N;
+        idx[3] = base + N + 1;
+        return;
+    }
+    int ci[4] = {i0, i0 + 1, i0, i0 + 1};
+    int cj[4] = {j0, j0, j0 + 1, j0 + 1};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         int ii = ci[q], jj = cj[q];

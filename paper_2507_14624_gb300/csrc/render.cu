@@ -16,7 +16,8 @@ using namespace trace;
 template <int RADF, int NRMF, bool COUNT, bool FLAT>
 __global__ void __launch_bounds__(256) render_kernel(GridDev g, ViewBatch vb, OutDev out, int persistent,
                                                      unsigned* tile_counter) {
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_view;
+    __shared__ ViewStart s_vs;  // the tile's view constants (all its rays start at the camera)
     const int tw = vb.tile_w, th = vb.tile_h;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wx = tw / 8;
@@ -25,21 +26,22 @@ __global__ void __launch_bounds__(256) render_kernel(GridDev g, ViewBatch vb, Ou
     unsigned long long acc[kNumCounters];
     if (COUNT)
         for (int q = 0; q < kNumCounters; ++q) acc[q] = 0;
-    int tile = blockIdx.x;
     for (;;) {
-        if (persistent) {
-            if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
-            __syncthreads();
-            tile = s_tile;
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            const int t = persistent ? (int)atomicAdd(tile_counter, 1u) : (int)blockIdx.x;
+            s_tile = t;
+            if (t < vb.total_tiles) {
+                const int vi = view_of_tile(vb.v, vb.n, t);
+                s_view = vi;
+                s_vs = view_start(g, make_float3(vb.v[vi].px, vb.v[vi].py, vb.v[vi].pz), g.nearest_probes != 0);
+            }
         }
+        __syncthreads();
+        const int tile = s_tile;
         if (tile >= vb.total_tiles) break;
-        // view of this tile: the last view whose first tile <= tile
-        int lo = 0, hi = vb.n - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (vb.v[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
-        }
+        const int lo = s_view;
+        const ViewStart vs = s_vs;
+        __syncthreads();  // s_* are rewritten by the next tile
         const ViewDev& v = vb.v[lo];
         int lt = tile - v.tile_begin;
         int x = (lt % v.tiles_x) * tw + lx, y = (lt / v.tiles_x) * th + ly;
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(256) render_kernel(GridDev g, ViewBatch vb, Ou
             r.w = make_float3(dx * il, dy * il, dz * il);
             Stats<COUNT> st;
             unsigned cells = 0, probes = 0;
-            PixelResult pr = trace_ray<RADF, NRMF, COUNT, FLAT>(g, r, st, cells, probes);
+            PixelResult pr = trace_ray<RADF, NRMF, COUNT, FLAT>(g, r, vs, st, cells, probes);
             long long o = v.out_offset + (long long)y * v.W + x;
             if (out.rgb) {
                 out.rgb[3 * o + 0] = pr.rgb.x;

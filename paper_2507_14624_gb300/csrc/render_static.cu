@@ -57,7 +57,8 @@ __global__ void fill_table_kernel(const __grid_constant__ TableChunk c, ViewDev*
 template <int RADF, int NRMF, bool COUNT>
 __global__ void __launch_bounds__(256) render_table_kernel(GridDev g, const ViewDev* __restrict__ views, int n_views,
                                                            int total_tiles, OutDev out, unsigned* queue) {
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_view;
+    __shared__ ViewStart s_vs;  // the tile's view constants (all its rays start at the camera)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wx = kTileW / 8;
     const int lx = (warp % wx) * 8 + (lane & 7), ly = (warp / wx) * 4 + (lane >> 3);
@@ -65,16 +66,21 @@ __global__ void __launch_bounds__(256) render_table_kernel(GridDev g, const View
     if (COUNT)
         for (int q = 0; q < kNumCounters; ++q) acc[q] = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        int tile = s_tile;
-        __syncthreads();
-        if (tile >= total_tiles) break;
-        int lo = 0, hi = n_views - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (views[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+        if (threadIdx.x == 0) {
+            const int t = (int)atomicAdd(queue, 1u);
+            s_tile = t;
+            if (t < total_tiles) {
+                const int vi = view_of_tile(views, n_views, t);
+                s_view = vi;
+                s_vs = view_start(g, make_float3(views[vi].px, views[vi].py, views[vi].pz), g.nearest_probes != 0);
+            }
         }
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= total_tiles) break;
+        const int lo = s_view;
+        const ViewStart vs = s_vs;
+        __syncthreads();  // s_* are rewritten by the next tile
         const ViewDev v = views[lo];
         int lt = tile - v.tile_begin;
         int x = (lt % v.tiles_x) * kTileW + lx, y = (lt / v.tiles_x) * kTileH + ly;
@@ -88,7 +94,7 @@ __global__ void __launch_bounds__(256) render_table_kernel(GridDev g, const View
             r.w = make_float3(dx * il, dy * il, dz * il);
             Stats<COUNT> st;
             unsigned cells = 0, probes = 0;
-            PixelResult pr = trace_ray<RADF, NRMF, COUNT, false>(g, r, st, cells, probes);
+            PixelResult pr = trace_ray<RADF, NRMF, COUNT, false>(g, r, vs, st, cells, probes);
             long long o = v.out_offset + (long long)y * v.W + x;
             if (out.rgb) {
                 out.rgb[3 * o + 0] = pr.rgb.x;

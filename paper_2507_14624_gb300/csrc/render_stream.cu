@@ -72,7 +72,7 @@ struct Lane {
 enum ColdF {
     kX0, kX1, kX2, kTin, kTout, kCut0, kCut1, kCut2, kSegA, kSegB,
     // segment fields used only when a walk descends, decides or ascends
-    kW0, kW1, kW2, kYa0, kYa1, kYa2, kCp, kTstar, kP00, kP01, kK0, kK1, kUend,
+    kW0, kW1, kW2, kYa0, kYa1, kYa2, kCp, kUstar, kP00, kP01, kK0, kK1, kUend,
     kUxc, kUyc, kUec,  // the low-resolution texel being refined: next crossings, exit
                        // (at a pending decision kUxc, kUyc hold the texel value and exit u)
     kNumColdF
@@ -235,7 +235,7 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     CF(kYa1) = s.Ya.y;
     CF(kYa2) = s.Ya.z;
     CF(kCp) = s.cp;
-    CF(kTstar) = s.tstar;
+    CF(kUstar) = s.ustar;
     CF(kP00) = s.p0[0];
     CF(kP01) = s.p0[1];
     CF(kK0) = s.k[0];
@@ -278,12 +278,6 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
 __device__ __forceinline__ float lane_tau(const Lane& L, float u) {
     float D = fmaf(-L.e, u, 1.0f);
     return D > 0.0f ? __fdividef(CF(kCp) * u, D) : kInf;
-}
-
-__device__ __forceinline__ float lane_r2(float tau) {
-    const float3 w = ray_w(), Ya = seg_Ya();
-    float x = fmaf(tau, w.x, Ya.x), y = fmaf(tau, w.y, Ya.y), z = fmaf(tau, w.z, Ya.z);
-    return x * x + y * y + z * z;
 }
 
 // Advance past the current texel (exit ue) over the earlier next boundary;
@@ -364,13 +358,9 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
         return;
     }
     if (L.level == 0) {  // candidate low-resolution texel
-        if (!g.two_way) {
-            float ta = lane_tau(L, L.u), tb = lane_tau(L, ue);
-            float dk = vmax * g.kappa;
-            if (lane_r2(fminf(fmaxf(CF(kTstar), ta), tb)) > dk * dk) {
-                L.mode = kUnknownRes;  // every full-resolution texel under it is passed behind
-                return;
-            }
+        if (!g.two_way && !comes_within(L.A0, L.A1, L.A2, L.e, CF(kUstar), L.u, ue, vmax * g.kappa)) {
+            L.mode = kUnknownRes;  // every full-resolution texel under it is passed behind
+            return;
         }
         CI(kI) = L.i;
         CI(kJ) = L.j;
@@ -415,10 +405,9 @@ template <int NRMF, bool COUNT>
 __device__ __forceinline__ void decide(const GridDev& g, Lane& L, Stats<COUNT>& st) {
     const int N = g.N;
     const float v = CF(kUxc), ue = CF(kUyc);
-    float ta = lane_tau(L, L.u), tb = lane_tau(L, ue);
-    float d = v, dk = d * g.kappa;
+    const float d = v;
     L.mode = kUnknownRes;
-    if (g.two_way || lane_r2(fminf(fmaxf(CF(kTstar), ta), tb)) <= dk * dk) {
+    if (g.two_way || comes_within(L.A0, L.A1, L.A2, L.e, CF(kUstar), L.u, ue, d * g.kappa)) {
         int i = L.i, j = L.j;
         LFP_CHECK_TEXEL(g.flags, (unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N, i, j);
         float2 no = NrmTexel<NRMF>::load(g.nrm, (size_t)L.probe * N * N + (size_t)j * N + i);
@@ -430,7 +419,7 @@ __device__ __forceinline__ void decide(const GridDev& g, Lane& L, Stats<COUNT>& 
             s.Ya = seg_Ya();
             s.w = w;
             s.A0 = L.A0;
-            float th = hit_time(s, ta, tb, d);
+            float th = hit_time(s, lane_tau(L, L.u), lane_tau(L, ue), d);
             float2 pp = oct_encode(fmaf(th, w.x, s.Ya.x), fmaf(th, w.y, s.Ya.y), fmaf(th, w.z, s.Ya.z));
             CI(kCls) = kHit;
             L.ux = 0.5f * (pp.x + 1.0f);  // shading uv
@@ -441,33 +430,7 @@ __device__ __forceinline__ void decide(const GridDev& g, Lane& L, Stats<COUNT>& 
 }
 
 // Traversal for fewer than 8 probes (Sec. 4.3): every probe, nearest to the
-// eye first (squared distances, ties to the lower index, the same arithmetic
-// as the loop-nest engine), as one pseudo-cell over [0, inf).
-__device__ __forceinline__ unsigned nearest_order(const GridDev& g, float3 X) {
-    const int P = g.nx * g.ny * g.nz;  // <= 8, checked at grid creation
-    float d2[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        float3 O = probe_pos(g, k < P ? k : 0);
-        float dx = __fsub_rn(X.x, O.x), dy = __fsub_rn(X.y, O.y), dz = __fsub_rn(X.z, O.z);
-        d2[k] = k < P ? __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) : kInf;
-    }
-    unsigned used = 0, order = 0;
-    for (int q = 0; q < P; ++q) {
-        int pick = -1;
-        float best = kInf;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (!(used >> k & 1u) && k < P && (pick < 0 || d2[k] < best)) {
-                best = d2[k];
-                pick = k;
-            }
-        used |= 1u << pick;
-        order |= (unsigned)pick << (3 * q);
-    }
-    return order;
-}
-
+// eye first (the view's order, view_start), as one pseudo-cell over [0, inf).
 __device__ __forceinline__ void nearest_start(unsigned order) {
     CI(kOrder) = (int)order;
     CI(kQ) = 0;
@@ -480,45 +443,16 @@ __device__ __forceinline__ void nearest_start(unsigned order) {
 // every lane computes and writes the same values).
 template <bool NEAREST>
 __device__ __forceinline__ void warp_view_setup(const GridDev& g, const ViewBatch& vb, int tile) {
-    int lo = 0, hi = vb.n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (vb.v[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
-    }
-    const ViewDev& v = vb.v[lo];
-    const float3 X = make_float3(v.px, v.py, v.pz);
-    // eye aligned with a probe: the nearest grid vertex within eye_eps
-    const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
-    const float og[3] = {g.ox, g.oy, g.oz}, Xa[3] = {X.x, X.y, X.z};
-    int iv[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) iv[q] = min(max((int)rintf(fdiv(Xa[q] - og[q], g.spacing)), 0), nc[q]);
-    const float3 O = corner_pos(g, iv[0], iv[1], iv[2], 0);
-    const float ex = X.x - O.x, ey = X.y - O.y, ez = X.z - O.z;
-    const bool eye = sqrtf(ex * ex + ey * ey + ez * ez) < g.eye_eps;
-    int inside = 0, c[3] = {0, 0, 0};
-    unsigned order = 0;
-    if (NEAREST) {
-        order = nearest_order(g, X);
-    } else {
-        // a camera in the closed probe box enters the grid at t = 0 for every
-        // direction, in the cell holding it (the arithmetic of ray_enter_grid)
-        inside = 1;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float lo_a = grid_plane(og[a], g.spacing, 0), hi_a = grid_plane(og[a], g.spacing, nc[a]);
-            if (!(Xa[a] >= lo_a && Xa[a] <= hi_a)) inside = 0;
-            c[a] = min(max((int)floorf(fdiv(Xa[a] - og[a], g.spacing)), 0), nc[a] - 1);
-        }
-        if (inside) order = cage_order(g, c[0], c[1], c[2], X);
-    }
-    WV(kWvView) = lo;
-    WV(kWvEye) = eye ? iv[0] + g.nx * (iv[1] + g.ny * iv[2]) : -1;
-    WV(kWvInside) = inside;
-    WV(kWvC0) = c[0];
-    WV(kWvC1) = c[1];
-    WV(kWvC2) = c[2];
-    WV(kWvOrder) = (int)order;
+    const int vi = view_of_tile(vb.v, vb.n, tile);
+    const ViewDev& v = vb.v[vi];
+    const ViewStart vs = view_start(g, make_float3(v.px, v.py, v.pz), NEAREST);
+    WV(kWvView) = vi;
+    WV(kWvEye) = vs.eye_probe;
+    WV(kWvInside) = vs.inside;
+    WV(kWvC0) = vs.c[0];
+    WV(kWvC1) = vs.c[1];
+    WV(kWvC2) = vs.c[2];
+    WV(kWvOrder) = (int)vs.order;
     __syncwarp();
 }
 

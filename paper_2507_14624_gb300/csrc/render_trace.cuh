@@ -48,6 +48,7 @@ struct Seg {
     float A0, A1, A2;  // |Ya + u V|^2 = A0 + u (A1 + u A2)
     float u_end;
     float tstar;       // closest approach to the probe (tau)
+    float ustar;       // the same point in u (0 before the segment, +inf past the octant's reach)
     int dir[2];        // motion of p_x, p_y with u
     int lo[2], hi[2];  // quadrant of the square (full-resolution indices)
 };
@@ -109,6 +110,21 @@ __device__ __forceinline__ void seg_setup(Seg& s, float3 Y0, float3 w, float ta,
     float te = tb - ta;
     s.u_end = (te < kInf) ? te * __frcp_rn(fmaf(e, te, cp)) : __frcp_rn(e);
     s.tstar = -(Ya.x * w.x + Ya.y * w.y + Ya.z * w.z) * __frcp_rn(w.x * w.x + w.y * w.y + w.z * w.z);
+    // u = tau / (cp + e tau) grows with tau wherever cp + e tau > 0, so the
+    // closest approach clamped to a tau-interval is u* clamped to its u-interval
+    const float Ls = fmaf(e, s.tstar, cp);
+    s.ustar = !(s.tstar > 0.0f) ? 0.0f : (Ls > 0.0f ? __fdividef(s.tstar, Ls) : kInf);
+}
+
+// Does the ray come within dk of the probe over the walk interval [u0, u1]?
+// min r = r(clamp(tau*, ta, tb)), and r^2 = |Ya + u V|^2 / (1 - e u)^2, so in
+// u it is A(uc) <= dk^2 D(uc)^2 at uc = clamp(u*, u0, u1): no division.
+__device__ __forceinline__ bool comes_within(float A0, float A1, float A2, float e, float ustar, float u0, float u1,
+                                             float dk) {
+    const float uc = fminf(fmaxf(ustar, u0), u1);
+    const float P = fmaf(fmaf(A2, uc, A1), uc, A0);
+    const float D = fmaf(-e, uc, 1.0f);
+    return P <= (dk * dk) * (D * D);
 }
 
 // u of the next boundary crossed along axis a from index i (full resolution)
@@ -208,15 +224,13 @@ __device__ bool fine_walk(const GridDev& g, const Seg& s, size_t pbase, float u0
         st.steps++;
         if (g.max_steps > 0 && (int)st.steps >= g.max_steps) { step_limited = true; return true; }
         if (!(Pa < d2 * D2a && Pb < d2 * D2b)) {  // the ray reaches the stored distance
-            float ta = tau_of(s, u), tb = tau_of(s, ue);
-            float dk = d * g.kappa;
             out.cls = kUnknown;  // unless the normal test passes below
-            if (g.two_way || r2_tau(s, fminf(fmaxf(s.tstar, ta), tb)) <= dk * dk) {
+            if (g.two_way || comes_within(s.A0, s.A1, s.A2, s.e, s.ustar, u, ue, d * g.kappa)) {
                 float2 no = NrmTexel<NRMF>::load(g.nrm, pbase + (size_t)jc * N + ic);
                 float3 n = oct_decode_unnorm(no.x, no.y);
                 if (COUNT) st.normal++;
                 if ((n.x * s.w.x + n.y * s.w.y + n.z * s.w.z) < 0.0f) {
-                    float th = hit_time(s, ta, tb, d);
+                    float th = hit_time(s, tau_of(s, u), tau_of(s, ue), d);
                     float2 pp = oct_encode(fmaf(th, s.w.x, s.Ya.x), fmaf(th, s.w.y, s.Ya.y), fmaf(th, s.w.z, s.Ya.z));
                     out.cls = kHit;
                     out.texel = i + N * j;
@@ -281,13 +295,9 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
         st.steps++;
         if (g.max_steps > 0 && (int)st.steps >= g.max_steps) { step_limited = true; return true; }
         if (!(Pa < d2 * D2a && Pb < d2 * D2b)) {  // candidate coarse texel
-            if (!g.two_way) {
-                float ta = tau_of(s, u), tb = tau_of(s, ue);
-                float dk = mm.y * g.kappa;
-                if (r2_tau(s, fminf(fmaxf(s.tstar, ta), tb)) > dk * dk) {
-                    out.cls = kUnknown;  // every full-resolution texel under it is passed behind
-                    return true;
-                }
+            if (!g.two_way && !comes_within(s.A0, s.A1, s.A2, s.e, s.ustar, u, ue, mm.y * g.kappa)) {
+                out.cls = kUnknown;  // every full-resolution texel under it is passed behind
+                return true;
             }
             // explicit multiply-adds: both engines round the start alike
             const float us = fine_start(s, d2, u, fmaf(-d2, D2a, Pa), ue, fmaf(-d2, D2b, Pb));
@@ -358,6 +368,90 @@ __device__ __forceinline__ unsigned cage_order(const GridDev& g, int c0, int c1,
            ((un ^ (m2 | m3)) << 18) | ((un ^ 7u) << 21);
 }
 
+// Traversal for fewer than 8 probes (Sec. 4.3): every probe ordered by the
+// squared distance to the eye X (ties to the lower index), corner of rank q
+// in bits [3q, 3q + 3).
+__device__ __forceinline__ unsigned nearest_order(const GridDev& g, float3 X) {
+    const int P = g.nx * g.ny * g.nz;  // <= 8, checked at grid creation
+    float d2[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        float3 O = probe_pos(g, k < P ? k : 0);
+        float dx = __fsub_rn(X.x, O.x), dy = __fsub_rn(X.y, O.y), dz = __fsub_rn(X.z, O.z);
+        d2[k] = k < P ? __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) : kInf;
+    }
+    unsigned used = 0, order = 0;
+    for (int q = 0; q < P; ++q) {
+        int pick = -1;
+        float best = kInf;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (!(used >> k & 1u) && k < P && (pick < 0 || d2[k] < best)) {
+                best = d2[k];
+                pick = k;
+            }
+        used |= 1u << pick;
+        order |= (unsigned)pick << (3 * q);
+    }
+    return order;
+}
+
+// Constants of a view's primary rays. They all start at the camera X, so
+// the eye-aligned test (Sec. 4.2), the grid entry when X lies in the closed
+// probe box (every direction enters at t = 0, in the cell holding X) and
+// that cell's cage order from X -- or, for the traversal with fewer than 8
+// probes, the nearest-probe order -- are the same for every ray of the
+// view: computed once per view or tile with the arithmetic the per-ray code
+// uses, so no decision changes.
+struct ViewStart {
+    int eye_probe;   // probe within eye_eps of X, else -1
+    int inside;      // grid traversal: X in the closed probe box
+    int c[3];        // the cell holding X
+    unsigned order;  // that cell's cage order from X, or the nearest-probe order
+};
+
+// nearest: the traversal for fewer than 8 probes (a compile-time constant
+// where the caller knows it, so the other branch folds away)
+__device__ __forceinline__ ViewStart view_start(const GridDev& g, float3 X, bool nearest) {
+    ViewStart vs;
+    const int nc[3] = {g.nx - 1, g.ny - 1, g.nz - 1};
+    const float og[3] = {g.ox, g.oy, g.oz}, Xa[3] = {X.x, X.y, X.z};
+    // eye aligned: the nearest grid vertex within eye_eps
+    int iv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) iv[a] = min(max((int)rintf(fdiv(Xa[a] - og[a], g.spacing)), 0), nc[a]);
+    const float3 O = corner_pos(g, iv[0], iv[1], iv[2], 0);
+    const float ex = X.x - O.x, ey = X.y - O.y, ez = X.z - O.z;
+    vs.eye_probe = sqrtf(ex * ex + ey * ey + ez * ez) < g.eye_eps ? iv[0] + g.nx * (iv[1] + g.ny * iv[2]) : -1;
+    vs.inside = 0;
+    vs.c[0] = vs.c[1] = vs.c[2] = 0;
+    vs.order = 0;
+    if (nearest) {
+        vs.order = nearest_order(g, X);
+        return vs;
+    }
+    int inside = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = grid_plane(og[a], g.spacing, 0), hi = grid_plane(og[a], g.spacing, nc[a]);
+        if (!(Xa[a] >= lo && Xa[a] <= hi)) inside = 0;
+        vs.c[a] = min(max((int)floorf(fdiv(Xa[a] - og[a], g.spacing)), 0), nc[a] - 1);
+    }
+    vs.inside = inside;
+    if (inside) vs.order = cage_order(g, vs.c[0], vs.c[1], vs.c[2], X);
+    return vs;
+}
+
+// View index of ray tile `tile`: the last view whose first tile <= tile.
+__device__ __forceinline__ int view_of_tile(const ViewDev* v, int n, int tile) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (v[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // traceOneProbe over [t0, t1]: split at the probe's axis planes (at most 4
 // single-octant segments, Sec. 4.2); the first non-MISS segment decides.
 template <int NRMF, bool COUNT, bool FLAT>
@@ -421,8 +515,9 @@ struct PixelResult {
     float3 rgb;
 };
 
+// vs: the constants of the ray's view (view_start at r.X).
 template <int RADF, int NRMF, bool COUNT, bool FLAT>
-__device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& st,
+__device__ PixelResult trace_ray(const GridDev& g, const Ray& r, const ViewStart& vs, Stats<COUNT>& st,
                                  unsigned& cells, unsigned& probes) {
     PixelResult res;
     res.cls = kMiss;
@@ -436,30 +531,23 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
 
     // Eye aligned with a probe (Sec. 4.2, Appendix A traceOneProbe): the
     // nearest grid vertex within eye_eps is looked up at oct(w) directly.
-    {
-        int iv[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) iv[a] = min(max((int)rintf(fdiv(Xa[a] - og[a], g.spacing)), 0), nc[a]);
-        int p = iv[0] + g.nx * (iv[1] + g.ny * iv[2]);
-        float3 O = probe_pos(g, p);
-        float dx = Xa[0] - O.x, dy = Xa[1] - O.y, dz = Xa[2] - O.z;
-        if (sqrtf(dx * dx + dy * dy + dz * dz) < g.eye_eps) {
-            float2 pp = oct_encode(r.w.x, r.w.y, r.w.z);
-            res.cls = kHit;
-            res.probe = p;
-            res.u = 0.5f * (pp.x + 1.0f);
-            res.v = 0.5f * (pp.y + 1.0f);
-            const int ti = texel_of(pp.x, g.N, 1), tj = texel_of(pp.y, g.N, 1);
-            res.texel = ti + g.N * tj;
-            if (g.eye_nearest) {  // the texel's own value: sample at its centre
-                res.u = (ti + 0.5f) / g.N;
-                res.v = (tj + 0.5f) / g.N;
-            }
-            res.rgb = shade<RADF>(g, p, res.u, res.v);
-            cells = 1;
-            probes = 1;
-            return res;
+    if (vs.eye_probe >= 0) {
+        const int p = vs.eye_probe;
+        float2 pp = oct_encode(r.w.x, r.w.y, r.w.z);
+        res.cls = kHit;
+        res.probe = p;
+        res.u = 0.5f * (pp.x + 1.0f);
+        res.v = 0.5f * (pp.y + 1.0f);
+        const int ti = texel_of(pp.x, g.N, 1), tj = texel_of(pp.y, g.N, 1);
+        res.texel = ti + g.N * tj;
+        if (g.eye_nearest) {  // the texel's own value: sample at its centre
+            res.u = (ti + 0.5f) / g.N;
+            res.v = (tj + 0.5f) / g.N;
         }
+        res.rgb = shade<RADF>(g, p, res.u, res.v);
+        cells = 1;
+        probes = 1;
+        return res;
     }
 
     // Fewer than 8 probes (Sec. 4.3): every probe, nearest to the eye first
@@ -467,26 +555,10 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
     // through to the next probe.
     if (g.nearest_probes) {
         const int P = g.nx * g.ny * g.nz;  // <= 8, checked at grid creation
-        float d2[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            float3 O = probe_pos(g, k < P ? k : 0);
-            float dx = __fsub_rn(Xa[0], O.x), dy = __fsub_rn(Xa[1], O.y), dz = __fsub_rn(Xa[2], O.z);
-            d2[k] = k < P ? __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) : kInf;
-        }
-        unsigned used = 0;
         bool saw_unknown = false, step_limited = false;
         cells = 1;
         for (int q = 0; q < P; ++q) {
-            int pick = -1;
-            float best = kInf;
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (!(used >> k & 1u) && k < P && (pick < 0 || d2[k] < best)) {
-                    best = d2[k];
-                    pick = k;
-                }
-            used |= 1u << pick;
+            const int pick = (vs.order >> (3 * q)) & 7;
             probes++;
             Decision dec;
             trace_probe<NRMF, COUNT, FLAT>(g, r, pick, probe_pos(g, pick), 0.0f, kInf, dec, st, step_limited);
@@ -509,28 +581,35 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
         return res;
     }
 
-    // Grid iterator (Sec. 4.3): 3D DDA over the cells the ray crosses.
-    float t_enter = 0.0f, t_exit = kInf;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float lo = grid_plane(og[a], g.spacing, 0), hi = grid_plane(og[a], g.spacing, nc[a]);
-        if (Wa[a] == 0.0f) {
-            if (Xa[a] < lo || Xa[a] > hi) t_enter = kInf;
-            continue;
-        }
-        float ta = fdiv(lo - Xa[a], Wa[a]), tb = fdiv(hi - Xa[a], Wa[a]);
-        if (ta > tb) { float x = ta; ta = tb; tb = x; }
-        t_enter = fmaxf(t_enter, ta);
-        t_exit = fminf(t_exit, tb);
-    }
-    if (!(t_enter <= t_exit)) return res;  // the ray misses the grid: MISS
+    // Grid iterator (Sec. 4.3): 3D DDA over the cells the ray crosses. A
+    // camera inside the probe box starts in its cell at t = 0 (from the view).
     int c[3], step[3];
+    if (vs.inside) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float p = fmaf(t_enter, Wa[a], Xa[a]);
-        c[a] = min(max((int)floorf(fdiv(p - og[a], g.spacing)), 0), nc[a] - 1);
-        step[a] = Wa[a] > 0.0f ? 1 : (Wa[a] < 0.0f ? -1 : 0);
+        for (int a = 0; a < 3; ++a) c[a] = vs.c[a];
+    } else {
+        float t_enter = 0.0f, t_exit = kInf;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float lo = grid_plane(og[a], g.spacing, 0), hi = grid_plane(og[a], g.spacing, nc[a]);
+            if (Wa[a] == 0.0f) {
+                if (Xa[a] < lo || Xa[a] > hi) t_enter = kInf;
+                continue;
+            }
+            float ta = fdiv(lo - Xa[a], Wa[a]), tb = fdiv(hi - Xa[a], Wa[a]);
+            if (ta > tb) { float x = ta; ta = tb; tb = x; }
+            t_enter = fmaxf(t_enter, ta);
+            t_exit = fminf(t_exit, tb);
+        }
+        if (!(t_enter <= t_exit)) return res;  // the ray misses the grid: MISS
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float p = fmaf(t_enter, Wa[a], Xa[a]);
+            c[a] = min(max((int)floorf(fdiv(p - og[a], g.spacing)), 0), nc[a] - 1);
+        }
     }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) step[a] = Wa[a] > 0.0f ? 1 : (Wa[a] < 0.0f ? -1 : 0);
     bool saw_unknown = false, step_limited = false;
     float t_in = 0.0f;
     for (int guard = 0; guard < nc[0] + nc[1] + nc[2] + 3; ++guard) {
@@ -555,7 +634,7 @@ __device__ PixelResult trace_ray(const GridDev& g, const Ray& r, Stats<COUNT>& s
         // cage: 8 corner probes, nearest to the entry point first, ties to
         // the lower probe index (corner k has index order k)
         float3 P = make_float3(fmaf(t_in, r.w.x, r.X.x), fmaf(t_in, r.w.y, r.X.y), fmaf(t_in, r.w.z, r.X.z));
-        const unsigned order = cage_order(g, c[0], c[1], c[2], P);
+        const unsigned order = (guard == 0 && vs.inside) ? vs.order : cage_order(g, c[0], c[1], c[2], P);
         int n_unknown = 0;
         for (int q = 0; q < 8; ++q) {
             Decision dec;

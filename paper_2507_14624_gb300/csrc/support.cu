@@ -121,17 +121,24 @@ __global__ void backward_warp_kernel(int N, int P, unsigned* flags, PixBatch pb,
          base += warps * 32) {
         long long q = base + lane;
         bool hit = false;
-        long long o = 0;
         int p = -1;
+        float u = 0.f, v = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
         if (q < total) {
             int lo = 0, hi = pb.n - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
                 if (pb.begin[mid] <= q) lo = mid; else hi = mid - 1;
             }
-            o = pb.out_offset[lo] + (q - pb.begin[lo]);
+            const long long o = pb.out_offset[lo] + (q - pb.begin[lo]);
+            // every pixel's saved state and gradient are valid memory: issue
+            // all loads at once (one round trip), use them for HIT pixels only
             p = aux_probe[o];
             hit = cls[o] == kHit;
+            u = aux_uv[2 * o];
+            v = aux_uv[2 * o + 1];
+            g0 = grad_rgb[3 * o];
+            g1 = grad_rgb[3 * o + 1];
+            g2 = grad_rgb[3 * o + 2];
             if (hit && (unsigned)p >= (unsigned)P) {  // not the saved state of a render of this grid
                 atomicOr(flags, kFlagBounds);
                 hit = false;
@@ -139,17 +146,15 @@ __global__ void backward_warp_kernel(int N, int P, unsigned* flags, PixBatch pb,
         }
         int idx[4];
         float w[4] = {0.f, 0.f, 0.f, 0.f};
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         if (hit) {
-            bilinear_taps(N, aux_uv[2 * o], aux_uv[2 * o + 1], idx, w);
+            bilinear_taps(N, u, v, idx, w);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 int zero = 0;
                 LFP_CHECK_TEXEL(flags, (unsigned)idx[k] < (unsigned)(N * N), idx[k], zero);
             }
-            g0 = grad_rgb[3 * o];
-            g1 = grad_rgb[3 * o + 1];
-            g2 = grad_rgb[3 * o + 2];
+        } else {
+            g0 = g1 = g2 = 0.f;
         }
         if (__ballot_sync(full, hit) == 0u) continue;
 #pragma unroll
