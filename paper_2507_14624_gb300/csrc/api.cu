@@ -157,6 +157,7 @@ GridDev grid_dev(const lfp_grid* g) {
     d.N = s.N;
     d.M = s.M;
     d.k = s.N / s.M;
+    d.kinv = (unsigned)(((1ull << 31) + (unsigned long long)d.k - 1) / (unsigned long long)d.k);
     d.two_way = s.thickness_rel < 0.0f ? 1 : 0;
     d.kappa = (float)(1.0 + 4.0 * (double)std::max(s.thickness_rel, 0.0f) / s.N);
     d.eye_eps = s.eye_eps > 0.0f ? s.eye_eps : 1e-6f * s.spacing;

@@ -27,6 +27,7 @@ struct GridDev {
     int nx, ny, nz;
     float ox, oy, oz, spacing;
     int N, M, k;              // k = N / M
+    unsigned kinv;            // ceil(2^31 / k): exact division by k of texel indices (div_k)
     float kappa;              // crossing threshold factor 1 + 4 th / N
     int two_way;              // th < 0: every crossing goes to the normal test
     float eye_eps;
@@ -202,6 +203,11 @@ template <> struct RadTexel<kF16> {
         return make_float3(a.x, a.y, b.x);
     }
 };
+
+// Exact x / k for 0 <= x < 8192 and 1 <= k <= 4096 by a multiply-high with
+// m = ceil(2^31 / k): x m / 2^31 = x / k + x e / 2^31 with 0 <= e < 1, and
+// x e / 2^31 < 1 / k whenever x k <= 2^31, so the floor is the quotient.
+__device__ __forceinline__ int div_k(unsigned kinv, int x) { return (int)__umulhi((unsigned)x << 1, kinv); }
 
 // Probe / cell-plane coordinate origin + spacing * b with two separate
 // roundings (no fused multiply-add), so a cell face and a probe plane at the

@@ -16,7 +16,7 @@ using namespace trace;
 template <int RADF, int NRMF, bool COUNT, bool FLAT>
 __global__ void __launch_bounds__(256) render_kernel(GridDev g, ViewBatch vb, OutDev out, int persistent,
                                                      unsigned* tile_counter) {
-    __shared__ int s_tile, s_view;
+    __shared__ int s_tile, s_view, s_x0, s_y0;
     __shared__ ViewStart s_vs;  // the tile's view constants (all its rays start at the camera)
     const int tw = vb.tile_w, th = vb.tile_h;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -34,17 +34,19 @@ __global__ void __launch_bounds__(256) render_kernel(GridDev g, ViewBatch vb, Ou
                 const int vi = view_of_tile(vb.v, vb.n, t);
                 s_view = vi;
                 s_vs = view_start(g, make_float3(vb.v[vi].px, vb.v[vi].py, vb.v[vi].pz), g.nearest_probes != 0);
+                const int lt = t - vb.v[vi].tile_begin;  // the tile's first pixel
+                s_x0 = (lt % vb.v[vi].tiles_x) * tw;
+                s_y0 = (lt / vb.v[vi].tiles_x) * th;
             }
         }
         __syncthreads();
         const int tile = s_tile;
         if (tile >= vb.total_tiles) break;
-        const int lo = s_view;
+        const int lo = s_view, x0 = s_x0, y0 = s_y0;
         const ViewStart vs = s_vs;
         __syncthreads();  // s_* are rewritten by the next tile
         const ViewDev& v = vb.v[lo];
-        int lt = tile - v.tile_begin;
-        int x = (lt % v.tiles_x) * tw + lx, y = (lt / v.tiles_x) * th + ly;
+        int x = x0 + lx, y = y0 + ly;
         if (x < v.W && y < v.H) {
             float a = ((x + 0.5f) / (float)v.W * 2.0f - 1.0f) * v.sa;
             float b = (1.0f - (y + 0.5f) / (float)v.H * 2.0f) * v.sb;

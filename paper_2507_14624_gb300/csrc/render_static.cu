@@ -57,7 +57,7 @@ __global__ void fill_table_kernel(const __grid_constant__ TableChunk c, ViewDev*
 template <int RADF, int NRMF, bool COUNT>
 __global__ void __launch_bounds__(256) render_table_kernel(GridDev g, const ViewDev* __restrict__ views, int n_views,
                                                            int total_tiles, OutDev out, unsigned* queue) {
-    __shared__ int s_tile, s_view;
+    __shared__ int s_tile, s_view, s_x0, s_y0;
     __shared__ ViewStart s_vs;  // the tile's view constants (all its rays start at the camera)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wx = kTileW / 8;
@@ -73,17 +73,19 @@ __global__ void __launch_bounds__(256) render_table_kernel(GridDev g, const View
                 const int vi = view_of_tile(views, n_views, t);
                 s_view = vi;
                 s_vs = view_start(g, make_float3(views[vi].px, views[vi].py, views[vi].pz), g.nearest_probes != 0);
+                const int lt = t - views[vi].tile_begin;  // the tile's first pixel
+                s_x0 = (lt % views[vi].tiles_x) * kTileW;
+                s_y0 = (lt / views[vi].tiles_x) * kTileH;
             }
         }
         __syncthreads();
         const int tile = s_tile;
         if (tile >= total_tiles) break;
-        const int lo = s_view;
+        const int lo = s_view, x0 = s_x0, y0 = s_y0;
         const ViewStart vs = s_vs;
         __syncthreads();  // s_* are rewritten by the next tile
         const ViewDev v = views[lo];
-        int lt = tile - v.tile_begin;
-        int x = (lt % v.tiles_x) * kTileW + lx, y = (lt / v.tiles_x) * kTileH + ly;
+        int x = x0 + lx, y = y0 + ly;
         if (x < v.W && y < v.H) {
             float a = ((x + 0.5f) / (float)v.W * 2.0f - 1.0f) * v.sa;
             float b = (1.0f - (y + 0.5f) / (float)v.H * 2.0f) * v.sb;

@@ -64,7 +64,7 @@ struct Lane {
     const float* dmap;   // this probe's distance map
     const float2* mmap;  // this probe's min/max map
     // walk
-    int level, i, j, lo0, hi0, lo1, hi1;
+    int level, i, j, lo0, lo1;  // index box: [lo, lo + span) per axis, span k (full res.) or M / 2
     float ux, uy, u, u1, Pa, D2a;  // after a HIT: (ux, uy) hold the shading uv
 };
 
@@ -93,7 +93,7 @@ __shared__ long long sh_o[kStreamThreads];  // output index of the lane's ray
 // to X), or the nearest-probe order of the traversal for fewer than 8
 // probes, are the same for all of its rays: they are computed once per tile
 // (same operations as per ray, so decisions do not change).
-enum WarpViewF { kWvView, kWvEye, kWvInside, kWvC0, kWvC1, kWvC2, kWvOrder, kWvNum };
+enum WarpViewF { kWvView, kWvEye, kWvInside, kWvC0, kWvC1, kWvC2, kWvOrder, kWvX0, kWvY0, kWvNum };
 __shared__ int sh_wv[kStreamThreads / 32][kWvNum];
 __device__ __forceinline__ int& WV(int f) { return sh_wv[threadIdx.x >> 5][f]; }
 
@@ -212,9 +212,7 @@ __device__ __forceinline__ void coarse_box(const GridDev& g, Lane& L) {
     const int hm = g.M / 2;
     const int quad = CI(kQuad);
     L.lo0 = (quad & 1) ? hm : 0;
-    L.hi0 = (quad & 1) ? g.M - 1 : hm - 1;
     L.lo1 = (quad & 2) ? hm : 0;
-    L.hi1 = (quad & 2) ? g.M - 1 : hm - 1;
 }
 
 // Segment segi: the octant line (same arithmetic as seg_setup) and the
@@ -263,8 +261,9 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     const int k = g.k, N = g.N;
     L.level = 0;
     coarse_box(g, L);
-    L.i = min(max(texel_of(s.p0[0], N, L.dir0) / k, L.lo0), L.hi0);
-    L.j = min(max(texel_of(s.p0[1], N, L.dir1) / k, L.lo1), L.hi1);
+    const int hm1 = g.M / 2 - 1;
+    L.i = min(max(div_k(g.kinv, texel_of(s.p0[0], N, L.dir0)), L.lo0), L.lo0 + hm1);
+    L.j = min(max(div_k(g.kinv, texel_of(s.p0[1], N, L.dir1)), L.lo1), L.lo1 + hm1);
     L.u = 0.0f;
     L.u1 = s.u_end;
     L.Pa = L.A0;
@@ -283,11 +282,11 @@ __device__ __forceinline__ float lane_tau(const Lane& L, float u) {
 // Advance past the current texel (exit ue) over the earlier next boundary;
 // false when the walk leaves the current level's index box. The axis is
 // selected into shared operands so both cases run the same instructions.
-__device__ __forceinline__ bool advance(Lane& L, int scale, float ue, float Pb, float D2b) {
+__device__ __forceinline__ bool advance(Lane& L, int scale, int span, float ue, float Pb, float D2b) {
     const bool xs = L.ux <= L.uy;
     const int dir = xs ? L.dir0 : L.dir1;
     const int c = (xs ? L.i : L.j) + dir;
-    if (c < (xs ? L.lo0 : L.lo1) || c > (xs ? L.hi0 : L.hi1)) return false;
+    if ((unsigned)(c - (xs ? L.lo0 : L.lo1)) >= (unsigned)span) return false;
     const float un = fmaxf(fmaf((float)((dir > 0 ? c + 1 : c) * scale), xs ? L.m0 : L.m1, xs ? L.q0 : L.q1), ue);
     if (xs) {
         L.i = c;
@@ -315,7 +314,7 @@ __device__ __forceinline__ void ascend(const GridDev& g, Lane& L) {
     float ue = CF(kUec);
     float Pb = fmaf(fmaf(L.A2, ue, L.A1), ue, L.A0);
     float Db = fmaf(-L.e, ue, 1.0f);
-    if (CI(kLastc) || !advance(L, g.k, ue, Pb, Db * Db)) L.mode = kSegEnd;
+    if (CI(kLastc) || !advance(L, g.k, g.M / 2, ue, Pb, Db * Db)) L.mode = kSegEnd;
 }
 
 // One texel visit (Appendix A low/highResolutionTracing, one step).
@@ -352,7 +351,7 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
     }
     float d2 = v * v;
     if (L.Pa < d2 * L.D2a && Pb < d2 * D2b) {  // the ray stays in front of the stored surface
-        if (!last && advance(L, L.level ? 1 : k, ue, Pb, D2b)) return;
+        if (!last && advance(L, L.level ? 1 : k, L.level ? k : M / 2, ue, Pb, D2b)) return;
         if (L.level) ascend(g, L);
         else L.mode = kSegEnd;
         return;
@@ -370,9 +369,7 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
         CI(kLastc) = last;
         L.level = 1;
         L.lo0 = L.i * k;
-        L.hi0 = L.lo0 + k - 1;
         L.lo1 = L.j * k;
-        L.hi1 = L.lo1 + k - 1;
         L.u1 = ue;
         {  // skip the full-resolution texels the ray passes in front of dmin (fine_start)
             Seg s;
@@ -386,8 +383,8 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
             L.D2a = Ds * Ds;
             L.u = us;
         }
-        L.i = min(max(texel_of(fmaf(CF(kK0), L.u, CF(kP00)), N, L.dir0), L.lo0), L.hi0);
-        L.j = min(max(texel_of(fmaf(CF(kK1), L.u, CF(kP01)), N, L.dir1), L.lo1), L.hi1);
+        L.i = min(max(texel_of(fmaf(CF(kK0), L.u, CF(kP00)), N, L.dir0), L.lo0), L.lo0 + k - 1);
+        L.j = min(max(texel_of(fmaf(CF(kK1), L.u, CF(kP01)), N, L.dir1), L.lo1), L.lo1 + k - 1);
         L.ux = L.dir0 == 0 ? kInf : fmaxf(fmaf((float)(L.dir0 > 0 ? L.i + 1 : L.i), L.m0, L.q0), L.u);
         L.uy = L.dir1 == 0 ? kInf : fmaxf(fmaf((float)(L.dir1 > 0 ? L.j + 1 : L.j), L.m1, L.q1), L.u);
         return;
@@ -453,6 +450,9 @@ __device__ __forceinline__ void warp_view_setup(const GridDev& g, const ViewBatc
     WV(kWvC1) = vs.c[1];
     WV(kWvC2) = vs.c[2];
     WV(kWvOrder) = (int)vs.order;
+    const int lt = tile - v.tile_begin;  // the tile's first pixel
+    WV(kWvX0) = (lt % v.tiles_x) * 8;
+    WV(kWvY0) = (lt / v.tiles_x) * 4;
     __syncwarp();
 }
 
@@ -461,8 +461,7 @@ __device__ __forceinline__ void warp_view_setup(const GridDev& g, const ViewBatc
 template <bool NEAREST>
 __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb, int tile, int slot, Lane& L) {
     const ViewDev& v = vb.v[WV(kWvView)];
-    int lt = tile - v.tile_begin;
-    int x = (lt % v.tiles_x) * 8 + (slot & 7), y = (lt / v.tiles_x) * 4 + (slot >> 3);
+    int x = WV(kWvX0) + (slot & 7), y = WV(kWvY0) + (slot >> 3);
     if (x >= v.W || y >= v.H) {
         L.mode = kIdle;  // outside a ragged view: no ray in this slot
         return;

@@ -109,7 +109,7 @@ __device__ __forceinline__ void seg_setup(Seg& s, float3 Y0, float3 w, float ta,
     s.A2 = V.x * V.x + V.y * V.y + V.z * V.z;
     float te = tb - ta;
     s.u_end = (te < kInf) ? te * __frcp_rn(fmaf(e, te, cp)) : __frcp_rn(e);
-    s.tstar = -(Ya.x * w.x + Ya.y * w.y + Ya.z * w.z) * __frcp_rn(w.x * w.x + w.y * w.y + w.z * w.z);
+    s.tstar = -(Ya.x * w.x + Ya.y * w.y + Ya.z * w.z);  // w is a unit vector (every caller normalises the ray)
     // u = tau / (cp + e tau) grows with tau wherever cp + e tau > 0, so the
     // closest approach clamped to a tau-interval is u* clamped to its u-interval
     const float Ls = fmaf(e, s.tstar, cp);
@@ -272,9 +272,10 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
         return fine_walk<NRMF, COUNT>(g, s, pbase, 0.0f, s.u_end, s.A0, 1.0f, s.lo[0], s.lo[1], s.hi[0], s.hi[1],
                                       out, st, step_limited);
     const float2* mip = g.mip + (size_t)probe * M * M;
-    int clo0 = s.lo[0] / k, chi0 = s.hi[0] / k, clo1 = s.lo[1] / k, chi1 = s.hi[1] / k;
-    int I = min(max(texel_of(s.p0[0], N, s.dir[0]) / k, clo0), chi0);
-    int J = min(max(texel_of(s.p0[1], N, s.dir[1]) / k, clo1), chi1);
+    int clo0 = div_k(g.kinv, s.lo[0]), chi0 = div_k(g.kinv, s.hi[0]);
+    int clo1 = div_k(g.kinv, s.lo[1]), chi1 = div_k(g.kinv, s.hi[1]);
+    int I = min(max(div_k(g.kinv, texel_of(s.p0[0], N, s.dir[0])), clo0), chi0);
+    int J = min(max(div_k(g.kinv, texel_of(s.p0[1], N, s.dir[1])), clo1), chi1);
     // coarse boundaries are full-resolution boundaries b = I k: same crossings
     float ux = s.dir[0] == 0 ? kInf : fmaxf(fmaf((float)((s.dir[0] > 0 ? I + 1 : I) * k), s.m[0], s.q[0]), 0.0f);
     float uy = s.dir[1] == 0 ? kInf : fmaxf(fmaf((float)((s.dir[1] > 0 ? J + 1 : J) * k), s.m[1], s.q[1]), 0.0f);
