@@ -8,10 +8,18 @@ HBM when the timed region starts, and L2 is flushed (a 256 MiB write) before
 every timed step, outside the timed kernel.
 
 Also reported: e2e (the same metric through the C ABI with host output
-buffers, copies inside the timed region), the roofline of the render kernel
-(algorithmic bytes from the kernel's own fetch counters), the FP64 oracle on
-the host cores (cpu_baseline), fwd+adjoint ms/view on the differentiable-fit
-views, and SM clocks sampled during the timed region.
+buffers, copies inside the timed region: the frame-loop rate of consecutive
+frames, see e2e.form), the roofline of the render kernel (algorithmic bytes
+from the kernel's own fetch counters, and the instruction-issue fraction
+from the committed ncu count), the FP64 oracle on the host cores
+(cpu_baseline), fwd+adjoint ms/view on the differentiable-fit views with its
+bytes and roofline fraction (fwd_adj; the adjoint alone under
+fwd_adj.backward), and SM clocks sampled during the timed region. The
+default line also carries "batched": the batched FP16 form (32 views, one
+persistent launch from a CUDA graph) with its own roofline, its ratio to the
+plain FP32 one-launch-per-view form on the same views
+(vs_single_view_fp32), and its forward + adjoint (--no-batched leaves it
+out).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lfp|reference]
                   [--workload room|batched|fit|few|multiscale|build|sweep|complexity]
