@@ -209,12 +209,15 @@ lfp_status lfp_render_ex(lfp_grid* grid, const lfp_view* views, int n_views,
                          const lfp_outputs* out, const lfp_render_opts* opts,
                          void* cuda_stream);
 
-/* Autotuner: time every launch configuration (streaming engine; loop-nest
- * engine with each ray-tile shape, one CTA per tile or persistent) on these
- * views, keep the fastest as the grid's default for calls that leave the
- * options zero, and return it in *best (may be NULL). Synchronises the
- * stream; the outputs (rgb and cls required) are overwritten with the last
- * run. Do not call it during stream capture. */
+/* Autotuner: time every launch configuration (streaming engine with each
+ * register budget, then the loop-nest engine with each ray-tile shape, one
+ * CTA per tile or persistent) on these views, keep the fastest as the grid's
+ * default for calls that leave the options zero, and return it in *best (may
+ * be NULL). A configuration whose first launch takes more than twice the
+ * best per-launch time so far is dropped after that launch; the others get
+ * a second warm-up and three timed launches. Synchronises the stream; the
+ * outputs (rgb and cls required) are overwritten with the last run. Do not
+ * call it during stream capture. */
 lfp_status lfp_autotune(lfp_grid* grid, const lfp_view* views, int n_views,
                         const lfp_outputs* out, lfp_render_opts* best, void* cuda_stream);
 

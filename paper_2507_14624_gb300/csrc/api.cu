@@ -596,22 +596,31 @@ lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const l
         cudaEventDestroy(e0);
         return LFP_ERR_CUDA;
     }
+    // Each candidate: one timed warm-up launch; a candidate whose warm-up
+    // took more than twice the best per-launch time so far is dropped (the
+    // streaming candidates come first and usually set that time), the others
+    // get one more warm-up and three timed launches.
     lfp_status st = LFP_OK;
     float best_ms = 3.4e38f;
     lfp_render_opts pick = cand[0];
+    auto timed = [&](const lfp_render_opts& k, int reps, float* ms) -> lfp_status {
+        if (cudaEventRecord(e0, s) != cudaSuccess) return LFP_ERR_CUDA;
+        for (int r = 0; r < reps; ++r) LFP_TRY(render_impl(g, views, n_views, out, &k, s));
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+            return LFP_ERR_CUDA;
+        return LFP_OK;
+    };
     for (const lfp_render_opts& k : cand) {
-        for (int w = 0; w < 2 && st == LFP_OK; ++w) st = render_impl(g, views, n_views, out, &k, s);
-        if (st != LFP_OK) break;
-        if (cudaEventRecord(e0, s) != cudaSuccess) { st = LFP_ERR_CUDA; break; }
-        for (int r = 0; r < 3 && st == LFP_OK; ++r) st = render_impl(g, views, n_views, out, &k, s);
         float ms = 0.f;
-        if (st != LFP_OK || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            if (st == LFP_OK) st = LFP_ERR_CUDA;
-            break;
-        }
-        if (ms < best_ms) {
-            best_ms = ms;
+        st = timed(k, 1, &ms);
+        if (st != LFP_OK) break;
+        if (ms > 2.0f * best_ms) continue;  // clearly slower: pruned
+        st = render_impl(g, views, n_views, out, &k, s);
+        if (st == LFP_OK) st = timed(k, 3, &ms);
+        if (st != LFP_OK) break;
+        if (ms / 3.0f < best_ms) {
+            best_ms = ms / 3.0f;
             pick = k;
         }
     }
