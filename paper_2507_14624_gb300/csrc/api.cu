@@ -22,7 +22,7 @@ struct lfp_grid {
     int device = 0;
     int sm_count = 0;
     float* dist = nullptr;
-    float2* mip = nullptr;
+    float* mip = nullptr;               // [P][2][M][M]: min plane, max plane per probe
     void* nrm = nullptr;
     void* rad = nullptr;
     unsigned* flags = nullptr;          // device flag word
@@ -446,7 +446,7 @@ lfp_status lfp_upload_probes(lfp_grid* g, int first_probe, int count, const lfp_
                                              g->desc.radiance_fmt, n, s));
         }
     }
-    LFP_CUDA(launch_build_mip(dist_dst, g->mip + (size_t)first_probe * g->desc.M * g->desc.M, count, N, g->desc.M, s));
+    LFP_CUDA(launch_build_mip(dist_dst, g->mip + (size_t)first_probe * 2 * g->desc.M * g->desc.M, count, N, g->desc.M, s));
     for (int p = first_probe; p < first_probe + count; ++p) g->uploaded[p] = 1;
     return LFP_OK;
 }
@@ -501,7 +501,7 @@ lfp_status lfp_build_probes_from_points(lfp_grid* g, int first_probe, int count,
         if (e != cudaSuccess) st = LFP_ERR_CUDA;
     }
     if (st == LFP_OK &&
-        launch_build_mip(g->dist + (size_t)first_probe * NN, g->mip + (size_t)first_probe * g->desc.M * g->desc.M,
+        launch_build_mip(g->dist + (size_t)first_probe * NN, g->mip + (size_t)first_probe * 2 * g->desc.M * g->desc.M,
                          count, N, g->desc.M, s) != cudaSuccess)
         st = LFP_ERR_CUDA;
     if (st == LFP_OK)

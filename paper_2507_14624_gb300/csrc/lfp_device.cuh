@@ -4,9 +4,12 @@
 //
 // Layout in HBM (one grid, P probes):
 //   dist [P][N][N]  f32           radial distance (Sec. 3, r_p)
-//   mip  [P][M][M]  float2        per-block (min, max) distance: the
-//                                 low-resolution map of Sec. 5.1, made
-//                                 conservative so skipping is exact
+//   mip  [P][2][M][M] f32         per-block min distance (plane 0) and max
+//                                 distance (plane 1): the low-resolution map
+//                                 of Sec. 5.1, made conservative so skipping
+//                                 is exact; the walk reads the min plane at
+//                                 every low-resolution visit and the max
+//                                 only at a candidate
 //   nrm  [P][N][N]  float2|half2  surface normal, octahedral-encoded
 //   rad  [P][N][N]  float4|half4  radiance RGB (+ pad), 16 / 8 bytes, so the
 //                                 two texels of one bilinear row are one
@@ -35,7 +38,7 @@ struct GridDev {
     int eye_nearest;          // eye-aligned lookup returns the texel holding oct(w)
     int nearest_probes;       // traversal for fewer than 8 probes (Sec. 4.3)
     const float* dist;
-    const float2* mip;
+    const float* mip;         // [P][2][M][M]
     const void* nrm;
     const void* rad;
     unsigned* flags;          // bit 0: step limit reached; bit 1: texel index out of range (checked builds)

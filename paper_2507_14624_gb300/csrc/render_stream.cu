@@ -61,8 +61,7 @@ struct Lane {
     // segment (see Seg): u-parametrised octant line, the fields the walk uses
     float e, m0, m1, q0, q1, A0, A1, A2;
     int dir0, dir1;
-    const float* dmap;   // this probe's distance map
-    const float2* mmap;  // this probe's min/max map
+    const float* plane;  // the current level's map: the probe's min plane (low resolution) or distance map
     // walk
     int level, i, j, lo0, lo1;  // index box: [lo, lo + span) per axis, span k (full res.) or M / 2
     float ux, uy, u, u1, Pa, D2a;  // after a HIT: (ux, uy) hold the shading uv
@@ -71,6 +70,7 @@ struct Lane {
 // control-round fields in shared memory
 enum ColdF {
     kX0, kX1, kX2, kTin, kTout, kCut0, kCut1, kCut2, kSegA, kSegB,
+    kY00, kY01, kY02,  // X - O of the current probe (probe_start), read by each segment set-up
     // segment fields used only when a walk descends, decides or ascends
     kW0, kW1, kW2, kYa0, kYa1, kYa2, kCp, kUstar, kP00, kP01, kK0, kK1, kUend,
     kUxc, kUyc, kUec,  // the low-resolution texel being refined: next crossings, exit
@@ -94,6 +94,8 @@ __shared__ long long sh_o[kStreamThreads];  // output index of the lane's ray
 // probes, are the same for all of its rays: they are computed once per tile
 // (same operations as per ray, so decisions do not change).
 enum WarpViewF { kWvView, kWvEye, kWvInside, kWvC0, kWvC1, kWvC2, kWvOrder, kWvX0, kWvY0, kWvNum };
+// the tile's camera factors: a of its 8 pixel columns, b of its 4 rows
+__shared__ float sh_wa[kStreamThreads / 32][8], sh_wb[kStreamThreads / 32][4];
 __shared__ int sh_wv[kStreamThreads / 32][kWvNum];
 __device__ __forceinline__ int& WV(int f) { return sh_wv[threadIdx.x >> 5][f]; }
 
@@ -192,6 +194,9 @@ __device__ __forceinline__ void probe_start(const GridDev& g, Lane& L) {
     L.probe = NEAREST ? kq : corner_index(g, CI(kC0), CI(kC1), CI(kC2), kq);
     float3 O = current_probe_pos<NEAREST>(g);
     const float3 X = ray_X(), w = ray_w();
+    CF(kY00) = X.x - O.x;
+    CF(kY01) = X.y - O.y;
+    CF(kY02) = X.z - O.z;
     const float t0 = CF(kTin), t1 = CF(kTout);
     float cx = w.x != 0.0f ? (O.x - X.x) * frcp(w.x) : kInf;
     float cy = w.y != 0.0f ? (O.y - X.y) * frcp(w.y) : kInf;
@@ -225,10 +230,8 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     CI(kSegFinal) = final_seg;
     if (final_seg) b = CF(kTout);
     CF(kSegB) = b;
-    float3 O = current_probe_pos<NEAREST>(g);
-    const float3 X = ray_X(), w = ray_w();
     Seg s;
-    seg_setup(s, make_float3(X.x - O.x, X.y - O.y, X.z - O.z), w, CF(kSegA), b, g.N);
+    seg_setup(s, make_float3(CF(kY00), CF(kY01), CF(kY02)), ray_w(), CF(kSegA), b, g.N);
     CF(kYa0) = s.Ya.x;
     CF(kYa1) = s.Ya.y;
     CF(kYa2) = s.Ya.z;
@@ -256,8 +259,7 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
         L.probe = p;
         (void)unused;
     }
-    L.dmap = g.dist + (size_t)L.probe * g.N * g.N;
-    L.mmap = g.mip + (size_t)L.probe * g.M * g.M;
+    L.plane = g.mip + (size_t)L.probe * 2 * g.M * g.M;
     const int k = g.k, N = g.N;
     L.level = 0;
     coarse_box(g, L);
@@ -305,6 +307,7 @@ __device__ __forceinline__ bool advance(Lane& L, int scale, int span, float ue, 
 // decision: continue the low-resolution walk after that texel.
 __device__ __forceinline__ void ascend(const GridDev& g, Lane& L) {
     L.level = 0;
+    L.plane = g.mip + (size_t)L.probe * 2 * g.M * g.M;
     L.i = CI(kI);
     L.j = CI(kJ);
     coarse_box(g, L);
@@ -327,19 +330,15 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
     float Pb = fmaf(fmaf(L.A2, ue, L.A1), ue, L.A0);
     float Db = fmaf(-L.e, ue, 1.0f);
     float D2b = Db * Db;
-    float v, vmax = 0.0f;
-    if (L.level) {
-        int i = L.i, j = L.j;
-        LFP_CHECK_TEXEL(g.flags, (unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N, i, j);
-        v = __ldg(L.dmap + (j * N + i));
-        if (COUNT) st.fine++;
-    } else {
-        int i = L.i, j = L.j;
-        LFP_CHECK_TEXEL(g.flags, (unsigned)i < (unsigned)M && (unsigned)j < (unsigned)M, i, j);
-        float2 mm = __ldg(L.mmap + (j * M + i));
-        v = mm.x;
-        vmax = mm.y;
-        if (COUNT) st.coarse++;
+    // both levels read one float of the current plane: the same load for
+    // every lane, whichever level it is on
+    const int R = L.level ? N : M;
+    int i = L.i, j = L.j;
+    LFP_CHECK_TEXEL(g.flags, (unsigned)i < (unsigned)R && (unsigned)j < (unsigned)R, i, j);
+    const float v = __ldg(L.plane + (j * R + i));
+    if (COUNT) {
+        if (L.level) st.fine++;
+        else st.coarse++;
     }
     if (COUNT) {  // the instrumented kernel also enforces the max_steps cap
         st.steps++;
@@ -357,7 +356,9 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
         return;
     }
     if (L.level == 0) {  // candidate low-resolution texel
-        if (!g.two_way && !comes_within(L.A0, L.A1, L.A2, L.e, CF(kUstar), L.u, ue, vmax * g.kappa)) {
+        // the block's max distance, from the max plane after the min plane
+        if (!g.two_way &&
+            !comes_within(L.A0, L.A1, L.A2, L.e, CF(kUstar), L.u, ue, __ldg(L.plane + (M + j) * M + i) * g.kappa)) {
             L.mode = kUnknownRes;  // every full-resolution texel under it is passed behind
             return;
         }
@@ -368,6 +369,7 @@ __device__ __forceinline__ void walk_step(const GridDev& g, Lane& L, Stats<COUNT
         CF(kUec) = ue;
         CI(kLastc) = last;
         L.level = 1;
+        L.plane = g.dist + (size_t)L.probe * N * N;
         L.lo0 = L.i * k;
         L.lo1 = L.j * k;
         L.u1 = ue;
@@ -451,8 +453,14 @@ __device__ __forceinline__ void warp_view_setup(const GridDev& g, const ViewBatc
     WV(kWvC2) = vs.c[2];
     WV(kWvOrder) = (int)vs.order;
     const int lt = tile - v.tile_begin;  // the tile's first pixel
-    WV(kWvX0) = (lt % v.tiles_x) * 8;
-    WV(kWvY0) = (lt / v.tiles_x) * 4;
+    const int x0 = (lt % v.tiles_x) * 8, y0 = (lt / v.tiles_x) * 4;
+    WV(kWvX0) = x0;
+    WV(kWvY0) = y0;
+    // pinhole factors of the tile's columns and rows (lanes 0-7 and 8-11),
+    // the arithmetic start_ray used per ray
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane < 8) sh_wa[w][lane] = ((x0 + lane + 0.5f) / (float)v.W * 2.0f - 1.0f) * v.sa;
+    else if (lane < 12) sh_wb[w][lane - 8] = (1.0f - (y0 + (lane - 8) + 0.5f) / (float)v.H * 2.0f) * v.sb;
     __syncwarp();
 }
 
@@ -466,8 +474,7 @@ __device__ __forceinline__ void start_ray(const GridDev& g, const ViewBatch& vb,
         L.mode = kIdle;  // outside a ragged view: no ray in this slot
         return;
     }
-    float a = ((x + 0.5f) / (float)v.W * 2.0f - 1.0f) * v.sa;
-    float b = (1.0f - (y + 0.5f) / (float)v.H * 2.0f) * v.sb;
+    const float a = sh_wa[threadIdx.x >> 5][slot & 7], b = sh_wb[threadIdx.x >> 5][slot >> 3];
     float dx = v.fx + a * v.rx + b * v.ux, dy = v.fy + a * v.ry + b * v.uy, dz = v.fz + a * v.rz + b * v.uz;
     float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
     const float3 X = make_float3(v.px, v.py, v.pz);

@@ -271,7 +271,7 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
     if (FLAT)  // Appendix A RayMarching: the full-resolution map only
         return fine_walk<NRMF, COUNT>(g, s, pbase, 0.0f, s.u_end, s.A0, 1.0f, s.lo[0], s.lo[1], s.hi[0], s.hi[1],
                                       out, st, step_limited);
-    const float2* mip = g.mip + (size_t)probe * M * M;
+    const float* mip = g.mip + (size_t)probe * 2 * M * M;  // min plane; the max plane follows it
     int clo0 = div_k(g.kinv, s.lo[0]), chi0 = div_k(g.kinv, s.hi[0]);
     int clo1 = div_k(g.kinv, s.lo[1]), chi1 = div_k(g.kinv, s.hi[1]);
     int I = min(max(div_k(g.kinv, texel_of(s.p0[0], N, s.dir[0])), clo0), chi0);
@@ -290,13 +290,14 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
         float D2b = Db * Db;
         int Ic = I, Jc = J;
         LFP_CHECK_TEXEL(g.flags, (unsigned)Ic < (unsigned)M && (unsigned)Jc < (unsigned)M, Ic, Jc);
-        float2 mm = __ldg(mip + (size_t)Jc * M + Ic);
-        float d2 = mm.x * mm.x;
+        const float dmin = __ldg(mip + (size_t)Jc * M + Ic);
+        float d2 = dmin * dmin;
         if (COUNT) st.coarse++;
         st.steps++;
         if (g.max_steps > 0 && (int)st.steps >= g.max_steps) { step_limited = true; return true; }
         if (!(Pa < d2 * D2a && Pb < d2 * D2b)) {  // candidate coarse texel
-            if (!g.two_way && !comes_within(s.A0, s.A1, s.A2, s.e, s.ustar, u, ue, mm.y * g.kappa)) {
+            if (!g.two_way &&
+                !comes_within(s.A0, s.A1, s.A2, s.e, s.ustar, u, ue, __ldg(mip + (size_t)(M + Jc) * M + Ic) * g.kappa)) {
                 out.cls = kUnknown;  // every full-resolution texel under it is passed behind
                 return true;
             }

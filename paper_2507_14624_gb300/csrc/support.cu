@@ -45,7 +45,7 @@ __global__ void convert_radiance_kernel(const float* __restrict__ rgb, void* __r
 }
 
 // one thread per coarse texel: min and max over its k x k block
-__global__ void build_mip_kernel(const float* __restrict__ dist, float2* __restrict__ mip, int count, int N, int M) {
+__global__ void build_mip_kernel(const float* __restrict__ dist, float* __restrict__ mip, int count, int N, int M) {
     long long total = (long long)count * M * M;
     int k = N / M;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total; c += (long long)gridDim.x * blockDim.x) {
@@ -60,7 +60,9 @@ __global__ void build_mip_kernel(const float* __restrict__ dist, float2* __restr
                 lo = fminf(lo, v);
                 hi = fmaxf(hi, v);
             }
-        mip[c] = make_float2(lo, hi);
+        float* page = mip + (size_t)p * 2 * M * M;  // this probe's min plane, then its max plane
+        page[rem] = lo;
+        page[(size_t)M * M + rem] = hi;
     }
 }
 
@@ -299,7 +301,7 @@ cudaError_t launch_convert_radiance(const float* rgb, void* rad, int rad_fmt, lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_build_mip(const float* dist, float2* mip, int count, int N, int M, cudaStream_t s) {
+cudaError_t launch_build_mip(const float* dist, float* mip, int count, int N, int M, cudaStream_t s) {
     long long total = (long long)count * M * M;
     build_mip_kernel<<<blocks_for(total), kThreads, 0, s>>>(dist, mip, count, N, M);
     return cudaGetLastError();
