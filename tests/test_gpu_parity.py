@@ -262,3 +262,34 @@ def test_fp16_texels_error_against_fp64(room):
     print("room fp16", st)
     assert st["class_match"] >= 0.999 and st["disagree"] <= 2e-3, st
     assert st["max_err"] <= 1e-3, st
+
+
+def test_mixed_view_batch_in_one_launch(tiny):
+    """One launch over views whose cameras sit inside the probe box, outside
+    it, exactly on a probe (eye aligned) and again inside: the per-view start
+    constants (eye test, first cell and its cage order) are taken once per
+    tile, so tiles of different views in one launch must each get their own.
+    Every view equals its own single-view launch and agrees with the oracle."""
+    sc, views, d, n, r = tiny
+    lfpk = _lfp()
+    P = sc.grid.probe_positions()
+    vs = [synth.random_view(sc, 600, 72, 40, 65.0),
+          synth.look_view((-0.35, 0.41, 0.57), 0.1, 0.05, 100.0, 57, 33),
+          synth.look_view(P[3], 0.7, 0.2, 70.0, 40, 24),
+          synth.random_view(sc, 601, 33, 65, 80.0),
+          synth.look_view((1.42, 1.37, -0.31), 3.6, 0.4, 90.0, 41, 17)]
+    g = make_grid(sc, d, n, r)
+    o = oracle.Oracle(sc.grid, d, n, r)
+    for engine in (lfpk.LFP_ENGINE_STREAM, lfpk.LFP_ENGINE_NESTED):
+        batch = g.render(vs, hit_texel=True, engine=engine, schedule=lfpk.LFP_SCHED_PERSISTENT)
+        off = 0
+        for v in vs:
+            single = g.render([v], hit_texel=True, engine=engine)
+            for k in ("cls", "probe", "texel", "rgb", "uv"):
+                assert torch.equal(batch[k][off:off + v.n_pixels], single[k]), (engine, k)
+            st = compare(single, o.render(v), sc.grid.N)
+            assert st["disagree"] <= max(2e-3, 1.0 / v.n_pixels) and st["max_err"] <= 1e-3, (engine, st)
+            off += v.n_pixels
+    eye = slice(sum(v.n_pixels for v in vs[:2]), sum(v.n_pixels for v in vs[:3]))
+    assert (batch["probe"][eye] == 3).all() and (batch["cls"][eye] == 1).all()
+    g.close()
