@@ -5,7 +5,11 @@ FP32 maps, 16x16 min/max map) rendering one 1920x1080 view at 70 deg, the
 configuration the headline metric (Mrays/s at 1080p) is quoted on. One step is
 one forward render of that view; inputs (probe maps, camera) are resident in
 HBM when the timed region starts, and L2 is flushed (a 256 MiB write) before
-every timed step, outside the timed kernel.
+every timed step, outside the timed kernel. Before timing, every workload
+runs the library's autotuner (lfp_autotune) on its views: it picks the skip
+level (the block side of the min/max map the walk skips with; the grid keeps
+block sides N/(4M), N/(2M), N/M and 2N/M) and the launch configuration, and
+the line reports the pick (autotuned, config.skip_block).
 
 Also reported: e2e (the same metric through the C ABI with host output
 buffers, copies inside the timed region: the frame-loop rate of consecutive
@@ -64,9 +68,12 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="room: leave out the batched FP16 form the default line carries as 'batched'")
     ap.add_argument("--occupancy", default="auto", choices=["auto", "8", "9"],
-                    help="batched / multiscale: the autotuner's launch configuration (default), or the streaming "
-                         "engine pinned to 8 blocks per SM (64 registers) or 9 (56 registers); the pinned forms "
-                         "are what the per-kernel ncu counts are taken on")
+                    help="the autotuner's launch configuration (default), or the streaming engine pinned to 8 "
+                         "blocks per SM (64 registers) or 9 (56 registers); the pinned forms are what the "
+                         "per-kernel ncu counts are taken on")
+    ap.add_argument("--skip-block", default="auto",
+                    help="the autotuner's skip level (default), or the block side of the min/max map the walk "
+                         "skips with (one of the grid's skip levels; multiscale: one per level, comma-separated)")
     return ap.parse_args()
 
 
@@ -155,16 +162,17 @@ def render_source_sha(workload="room"):
     return h.hexdigest()[:16]
 
 
-def ncu_summary(workload, occ=None):
+def ncu_summary(workload, occ=None, skip=None):
     """The committed ncu summary of the render kernel for this workload, if it
-    was taken on the current kernel source; else an empty dict. Summaries
-    taken per register budget of the streaming engine keep them under
-    "by_occupancy"; `occ` ("8" or "9") selects one."""
+    was taken on the current kernel source and at the skip level `skip` (the
+    block side the walk skipped with; multiscale: a list, one per level);
+    else an empty dict. Summaries taken per register budget of the streaming
+    engine keep them under "by_occupancy"; `occ` ("8" or "9") selects one."""
     p = os.path.join(ROOT, "profiles", f"render_{workload}_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        if d.get("source_sha") == render_source_sha(workload):
+        if d.get("source_sha") == render_source_sha(workload) and d.get("skip_block") == skip:
             if "by_occupancy" in d:
                 return d["by_occupancy"].get(occ, {}) if occ else {}
             return d
@@ -186,18 +194,18 @@ def occupancy_key(pinned, tuned):
     return "9" if tuned.get("occupancy") == 2 else "8"  # LFP_OCC_9
 
 
-def ncu_traffic(workload, occ=None):
+def ncu_traffic(workload, occ=None, skip=None):
     """DRAM bytes per launch (read + write) from the committed ncu summary, or None."""
-    d = ncu_summary(workload, occ)
+    d = ncu_summary(workload, occ, skip)
     return float(d["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in d else None
 
 
-def issue_roofline(workload, ms_launch, sm_mhz, n_sm, occ=None):
+def issue_roofline(workload, ms_launch, sm_mhz, n_sm, occ=None, skip=None):
     """The kernel is bound by instruction issue: warp instructions per launch
     (an ncu count on the current source and register budget) over the
     event-timed launch, against n_sm x 4 schedulers x one warp instruction per
     clock."""
-    d = ncu_summary(workload, occ)
+    d = ncu_summary(workload, occ, skip)
     if "warp_inst_per_launch" not in d or not sm_mhz:
         return None
     achieved = d["warp_inst_per_launch"] / (ms_launch / 1e3) / 1e9
@@ -254,13 +262,15 @@ def measure(args, workload, rank, world, local, with_cpu=True):
     grid.upload(d, n, r)
     sched = lfpk.LFP_SCHED_PERSISTENT if len(views) > 1 else 0
     tuned = None
-    pin_engine, pin_occ = 0, 0  # 0: the grid's default (autotuned for the batched form)
+    pin_engine, pin_occ = 0, 0  # 0: the grid's default (autotuned)
+    pin_skip = 0 if args.skip_block == "auto" else int(args.skip_block)
     if args.occupancy != "auto":
         pin_engine, pin_occ = lfpk.LFP_ENGINE_STREAM, OCCUPANCY[args.occupancy]
         sched = 0
-    elif len(views) > 1:  # the batched form: launch configuration picked by the autotuner
+    else:  # launch configuration and skip level picked by the autotuner
         tuned = grid.autotune(views)
         sched = 0
+    skip = pin_skip or (tuned["skip_block"] if tuned else sc.grid.N // sc.grid.M)
     occ_key = occupancy_key(args.occupancy, tuned)
     arr, nv, total = lfpk.make_views(views)
     dev = torch.device("cuda", local)
@@ -270,7 +280,7 @@ def measure(args, workload, rank, world, local, with_cpu=True):
     outs.rgb, outs.cls = rgb.data_ptr(), cls.data_ptr()
     opts = lfp.lfp_render_opts()
     opts.schedule = sched
-    opts.engine, opts.occupancy = pin_engine, pin_occ
+    opts.engine, opts.occupancy, opts.skip_block = pin_engine, pin_occ, pin_skip
     stream = torch.cuda.current_stream()
     sh = lfpk._stream_handle(stream)
     launches_per_step = (nv + 127) // 128
@@ -280,7 +290,7 @@ def measure(args, workload, rank, world, local, with_cpu=True):
 
     graph = None
     if len(views) > 1:  # the batched form: one persistent launch replayed from a CUDA graph
-        graph, gout = grid.render_graph(views, aux=False, engine=pin_engine, occupancy=pin_occ)
+        graph, gout = grid.render_graph(views, aux=False, engine=pin_engine, occupancy=pin_occ, skip_block=pin_skip)
         rgb, cls = gout["rgb"], gout["cls"]
         outs.rgb, outs.cls = rgb.data_ptr(), cls.data_ptr()
 
@@ -346,13 +356,13 @@ def measure(args, workload, rank, world, local, with_cpu=True):
 
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (ms_launch / 1e3) / 1e9
-    traffic = ncu_traffic(workload, occ_key)
+    traffic = ncu_traffic(workload, occ_key, skip)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": int(alg_bytes), "kernel": kernel_of(workload),
                 "counters_per_launch": counters,
                 "issue": issue_roofline(workload, ms_launch, clk.get("sm_mhz"),
-                                        torch.cuda.get_device_properties(dev).multi_processor_count, occ_key)}
+                                        torch.cuda.get_device_properties(dev).multi_processor_count, occ_key, skip)}
 
     extra = {}
     if not args.no_adjoint and rank == 0:
@@ -374,7 +384,7 @@ def measure(args, workload, rank, world, local, with_cpu=True):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_launch, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f16+f32" if f16 else "f32", "data": "synthetic (seeded analytic scene, probe maps ray-cast)",
-            "config": workload_info(workload, views, sc.grid), "e2e": e2e,
+            "config": dict(workload_info(workload, views, sc.grid), skip_block=skip), "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "cuda_graph": graph is not None,
             "autotuned": tuned, "occupancy": args.occupancy if args.occupancy != "auto" else occ_key,
             "roofline": roofline, "clocks": clk,
@@ -418,6 +428,9 @@ def single_view_fp32(torch, lfpk, lfp, sc, views, d, n, r, cls_f16, flush, batch
     the class agreement of the FP16 batched images with the FP32 ones."""
     g = lfpk.ProbeGrid(sc.grid)
     g.upload(d, n, r)
+    # the plain form gets its own launch configuration and skip level, tuned
+    # on its largest view as it runs (one view per launch)
+    g.autotune([max(views, key=lambda v: v.W * v.H)])
     dev = cls_f16.device
     total = sum(v.W * v.H for v in views)
     rgb = torch.empty((total, 3), dtype=torch.float32, device=dev)
@@ -545,6 +558,7 @@ def fwd_adjoint_fit(torch, lfpk, lfp, dev, peak, steps=5):
     d, n, r = sc.probe_maps()
     g = lfpk.ProbeGrid(sc.grid)
     g.upload(d, n, r)
+    g.autotune(views)
     res = fwd_adjoint(torch, lfp, g, views, dev, False, peak, "fit",
                       "fit: room grid seed 4, 64 views 800x800, forward with saved state + adjoint", steps=steps,
                       schedule=lfpk.LFP_SCHED_PERSISTENT)
@@ -652,10 +666,17 @@ def run_multiscale(args):
     pin_engine, pin_occ = 0, 0  # 0: each level's default (autotuned)
     if args.occupancy != "auto":
         pin_engine, pin_occ = lfpk.LFP_ENGINE_STREAM, OCCUPANCY[args.occupancy]
+    pins = [0] * len(h.grids) if args.skip_block == "auto" else [int(x) for x in args.skip_block.split(",")]
+    skips = []
     for k, g in enumerate(h.grids):  # each level's launch configuration from the autotuner
         mine = [v for v, l in zip(views, lev) if l == k]
         if mine and args.occupancy == "auto":
             tuned[str(k)] = g.autotune(mine)
+        if pins[k]:  # a pinned skip level becomes the level's default
+            o = lfp.lfp_render_opts()
+            o.skip_block = pins[k]
+            lfp.lfp_set_defaults(g.handle, o)
+        skips.append(pins[k] or tuned.get(str(k), {}).get("skip_block") or g.N // g.M)
     graph, out = h.render_graph(views, aux=False, engine=pin_engine, occupancy=pin_occ)
 
     cnt = torch.zeros(lfp.N_COUNTERS, dtype=torch.int64, device=dev)
@@ -737,7 +758,7 @@ def run_multiscale(args):
     # ncu counts were taken per level and register budget on a 9-view run of
     # the same levels (per ray, scaled to this step's rays of each level, with
     # the budget each level ran with); per launch = per step / launches
-    summ = ncu_summary("multiscale").get("levels", {})
+    summ = ncu_summary("multiscale", skip=skips).get("levels", {})
     kernels, inst, dram = {}, 0.0, 0.0
     for k in sorted(set(lev)):
         rays_k = sum(v.W * v.H for v, l in zip(views, lev) if l == k)
@@ -785,7 +806,8 @@ def run_multiscale(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32",
                 "data": "synthetic (seeded street-grid scene, probe maps ray-cast)",
                 "config": {"workload": MULTISCALE_DESC, "views": len(views), "rays_per_step": int(total),
-                           "views_per_level": per_level, "l2": "flushed before every timed step (256 MiB write)"},
+                           "views_per_level": per_level, "skip_blocks": skips,
+                           "l2": "flushed before every timed step (256 MiB write)"},
                 "e2e": {"value": round(e2e_value, 3), "unit": "Mrays/s", "h2d_bytes_per_step": int(nv * 72),
                         "d2h_bytes_per_step": int(total * 13)},
                 "gpu_launches": launches_per_step * args.steps, "cuda_graph": True, "autotuned": tuned,
@@ -1161,6 +1183,7 @@ def run_fit(args):
     g = lfpk.ProbeGrid(sc.grid)
     g.upload(d, n, r)
     mine = fit.shard_views(views, rank, world)  # data parallel: one gradient all-reduce per step
+    g.autotune(mine)
     total = sum(v.W * v.H for v in views)
     targets = fit.make_targets(g, mine, sigma=0.01, seed=404 + rank)
     fit.fit_radiance(g, mine, targets, steps=args.warmup, lr=1e-2, seed=404, total_pixels=total)

@@ -77,6 +77,9 @@ enum {
  *   origin, spacing > 0      probe (0,0,0) position and grid pitch
  *   N                        full-resolution map side, even, 2..8192
  *   M                        low-resolution map side, even, N % M == 0, M <= N
+ *                            (blocks of k = N / M texels; the grid keeps the
+ *                            min/max maps of a few more block sides for the
+ *                            walk to skip with: lfp_skip_blocks)
  *   radiance_fmt, normal_fmt device storage of radiance (RGB) and normals
  *                            (octahedral-encoded RG); distance is always float32
  *   thickness_rel            th: a texel crossing counts while the ray's
@@ -178,6 +181,9 @@ typedef struct {
                        threads per SM, up to 64 registers per thread) or
                        LFP_OCC_9 (9 blocks, up to 56 registers); identical
                        results, different speed per workload */
+    int skip_block; /* side, in full-resolution texels, of the min/max
+                       blocks the walk skips over: one of lfp_skip_blocks,
+                       or 0 for the grid's default. Both engines. */
 } lfp_render_opts;
 enum { LFP_OCC_AUTO = 0, LFP_OCC_8 = 1, LFP_OCC_9 = 2 };
 
@@ -187,7 +193,7 @@ enum { LFP_OCC_AUTO = 0, LFP_OCC_8 = 1, LFP_OCC_9 = 2 };
 lfp_status lfp_create_grid(const lfp_grid_desc* desc, lfp_grid** out);
 
 /* Upload maps for probes [first_probe, first_probe + count) and rebuild their
- * low-resolution min/max maps (Sec. 5.1). Host planes are copied before the
+ * low-resolution min/max maps (Sec. 5.1) at every skip level. Host planes are copied before the
  * call returns only if the stream is synchronous; otherwise they must stay
  * valid until the stream has run the copy. Errors: INVALID_ARG, OOM, CUDA. */
 lfp_status lfp_upload_probes(lfp_grid* grid, int first_probe, int count,
@@ -209,13 +215,15 @@ lfp_status lfp_render_ex(lfp_grid* grid, const lfp_view* views, int n_views,
                          const lfp_outputs* out, const lfp_render_opts* opts,
                          void* cuda_stream);
 
-/* Autotuner: time every launch configuration (streaming engine with each
- * register budget, then the loop-nest engine with each ray-tile shape, one
- * CTA per tile or persistent) on these views, keep the fastest as the grid's
- * default for calls that leave the options zero, and return it in *best (may
- * be NULL). A configuration whose first launch takes more than twice the
- * best per-launch time so far is dropped after that launch; the others get
- * a second warm-up and three timed launches. Synchronises the stream; the
+/* Autotuner: first the skip level (lfp_skip_blocks), timed on the
+ * streaming engine with the 8-block register budget; then, at that level,
+ * every launch configuration (streaming engine with each register budget,
+ * the loop-nest engine with each ray-tile shape, one CTA per tile or
+ * persistent) on these views. Keeps the fastest as the grid's default for
+ * calls that leave the options zero, and returns it in *best (may be
+ * NULL). A configuration whose first launch takes more than twice the best
+ * per-launch time so far is dropped after that launch; the others get a
+ * second warm-up and three timed launches. Synchronises the stream; the
  * outputs (rgb and cls required) are overwritten with the last run. Do not
  * call it during stream capture. */
 lfp_status lfp_autotune(lfp_grid* grid, const lfp_view* views, int n_views,
@@ -225,7 +233,8 @@ lfp_status lfp_autotune(lfp_grid* grid, const lfp_view* views, int n_views,
  * with the one it picks (e.g. a pick it returned earlier for the same views
  * and GPU, kept by the caller). Fields left zero keep the current default;
  * march must be LFP_MARCH_HIER. Host-only, no stream. Errors: INVALID_ARG
- * (a field out of range or an invalid tile shape). */
+ * (a field out of range, an invalid tile shape, or a skip_block that is not
+ * one of the grid's skip levels). */
 lfp_status lfp_set_defaults(lfp_grid* grid, const lfp_render_opts* opts);
 
 /* Render into HOST memory: one call that runs lfp_render on device buffers
@@ -289,9 +298,26 @@ lfp_status lfp_set_radiance(lfp_grid* grid, const float* dev_radiance_f32, void*
  * some ray reached max_steps, else LFP_OK. */
 lfp_status lfp_check_flags(lfp_grid* grid, void* cuda_stream);
 
-/* Device bytes the grid's probe storage takes for a descriptor (maps + mip),
- * the byte accounting of Sec. 6 (memory efficient representation). */
+/* Device bytes the grid's probe storage takes for a descriptor (maps and
+ * the min/max maps of every skip level), the byte accounting of Sec. 6
+ * (memory efficient representation). */
 lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes);
+
+/* Skip levels (Sec. 5.1 hierarchical tracing; the paper uses one
+ * low-resolution map and studies its size in Sec. 6). Besides the
+ * descriptor's map of blocks of k = N / M full-resolution texels, a grid
+ * keeps per-block min/max maps at the block sides k / 4, k / 2 and 2 k,
+ * those of them that are whole numbers >= 2 and cut the map into an even
+ * number of blocks per side; all are rebuilt by every upload. The walk
+ * skips over the blocks of one level (lfp_render_opts.skip_block; the
+ * grid's default is k until lfp_autotune or lfp_set_defaults picks
+ * another). A block is skipped only while the ray stays in front of its
+ * minimum, so every level finds the same crossings: the level changes the
+ * speed, while classes and colours agree to rounding of the walk's start
+ * inside a block. Writes the block sides, ascending, to blocks[0 .. *count)
+ * (room for LFP_MAX_SKIP_LEVELS ints). Host-only. Errors: INVALID_ARG. */
+#define LFP_MAX_SKIP_LEVELS 4
+lfp_status lfp_skip_blocks(const lfp_grid_desc* desc, int* blocks, int* count);
 
 /* Most views one lfp_render_static call accepts. */
 #define LFP_STATIC_MAX_VIEWS 4096
@@ -388,8 +414,9 @@ lfp_status lfp_read_probes(lfp_grid* grid, int first_probe, int count, float* di
  * lfp_pick_levels writes that level for each view (host int32[n_views]).
  * lfp_render_levels renders every view with its level into the shared flat
  * outputs (each view at its own out_offset): one lfp_render_ex call per
- * level that has views, on `cuda_stream`, same options; aux_probe indexes the
- * probes of the view's level. lfp_render_backward_levels is the adjoint:
+ * level that has views, on `cuda_stream`, same options (a nonzero skip_block
+ * must be a skip level of every level that has views; 0 takes each grid's
+ * default); aux_probe indexes the probes of the view's level. lfp_render_backward_levels is the adjoint:
  * grad_radiance is a host array of n_levels device pointers, entry k the
  * [P_k][N_k][N_k][3] f32 accumulator of level k (may be NULL for a level no
  * view uses); each level's views go to lfp_render_backward_ex.

@@ -127,6 +127,11 @@ class ProbeGrid:
     def device_bytes(self) -> int:
         return lfp.lfp_grid_bytes(self.desc)
 
+    @property
+    def skip_blocks(self) -> list:
+        """Block sides of the grid's skip levels (lfp_skip_blocks), ascending."""
+        return lfp.lfp_skip_blocks(self.desc)
+
     def upload(self, dist, normal, radiance, first_probe=0, stream=None):
         """Upload probe maps (numpy float32 host arrays or CUDA float32 tensors):
         dist [P][N][N], normal [P][N][N][3], radiance [P][N][N][3]."""
@@ -196,10 +201,11 @@ class ProbeGrid:
         lfp.lfp_set_radiance(self.handle, ctypes.c_void_p(r.data_ptr()), _stream_handle(stream))
 
     def render(self, views, aux=True, hit_texel=False, counters=False, march=LFP_MARCH_HIER, tile=None,
-               schedule=0, engine=0, occupancy=0, stream=None):
+               schedule=0, engine=0, occupancy=0, skip_block=0, stream=None):
         """Render views; returns a dict of CUDA tensors: rgb [P,3] f32,
         cls [P] u8, and optionally probe [P] i32, uv [P,2] f32, texel [P] i32,
-        counters [8] i64 (see lfp.COUNTER_NAMES)."""
+        counters [8] i64 (see lfp.COUNTER_NAMES). skip_block: one of
+        skip_blocks, 0 for the grid's default."""
         import torch
         arr, n, total = make_views(views)
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -225,6 +231,7 @@ class ProbeGrid:
         opts.schedule = schedule
         opts.engine = engine
         opts.occupancy = occupancy
+        opts.skip_block = skip_block
         lfp.lfp_render_ex(self.handle, arr, n, o, opts, _stream_handle(stream))
         return out
 
@@ -241,6 +248,7 @@ class ProbeGrid:
                 opts = lfp.lfp_render_opts()
                 opts.engine, opts.schedule, opts.occupancy = got["engine"], got["schedule"], got["occupancy"]
                 opts.tile_w, opts.tile_h = got["tile"]
+                opts.skip_block = got.get("skip_block", 0)
                 lfp.lfp_set_defaults(self.handle, opts)
                 return dict(got, tile=tuple(got["tile"]), cached=True)
         arr, n, total = make_views(views)
@@ -250,21 +258,23 @@ class ProbeGrid:
         o = lfp.lfp_outputs()
         o.rgb, o.cls = rgb.data_ptr(), cls.data_ptr()
         b = lfp.lfp_autotune(self.handle, arr, n, o, _stream_handle(stream))
-        pick = {"engine": b.engine, "tile": (b.tile_w, b.tile_h), "schedule": b.schedule, "occupancy": b.occupancy}
+        pick = {"engine": b.engine, "tile": (b.tile_w, b.tile_h), "schedule": b.schedule, "occupancy": b.occupancy,
+                "skip_block": b.skip_block}
         if cache:
             _write_tune_cache(cache, key, pick)
         return pick
 
-    def render_graph(self, views, aux=False, engine=0, occupancy=0, stream=None):
+    def render_graph(self, views, aux=False, engine=0, occupancy=0, skip_block=0, stream=None):
         """Capture one render of these views in a CUDA graph (outputs are
         preallocated and reused). Returns (graph, outputs); graph.replay()
-        re-renders into the same tensors. engine / occupancy as in render
-        (0: the grid's default)."""
+        re-renders into the same tensors. engine / occupancy / skip_block as
+        in render (0: the grid's default)."""
         import torch
         s = torch.cuda.Stream() if stream is None else stream
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            out = self.render(views, aux=aux, engine=engine, occupancy=occupancy, stream=s)  # warm-up outside capture
+            out = self.render(views, aux=aux, engine=engine, occupancy=occupancy, skip_block=skip_block,
+                              stream=s)  # warm-up outside capture
         torch.cuda.current_stream().wait_stream(s)
         arr, n, total = make_views(views)
         o = lfp.lfp_outputs()
@@ -274,6 +284,7 @@ class ProbeGrid:
         opts = lfp.lfp_render_opts()
         opts.engine = engine
         opts.occupancy = occupancy
+        opts.skip_block = skip_block
         graph = torch.cuda.CUDAGraph()
         keep = (arr, o, opts)
         with torch.cuda.graph(graph, stream=s):

@@ -22,7 +22,12 @@ struct lfp_grid {
     int device = 0;
     int sm_count = 0;
     float* dist = nullptr;
-    float* mip = nullptr;               // [P][2][M][M]: min plane, max plane per probe
+    // min/max maps per skip level (lfp_skip_blocks), block side skip_k[l],
+    // each [P][2][M'][M'] with M' = N / skip_k[l]: min plane, max plane per probe
+    int n_skip = 0;
+    int skip_k[LFP_MAX_SKIP_LEVELS] = {};
+    float* skip_mip[LFP_MAX_SKIP_LEVELS] = {};
+    int skip = 0;                       // default skip level (lfp_autotune, lfp_set_defaults)
     void* nrm = nullptr;
     void* rad = nullptr;
     unsigned* flags = nullptr;          // device flag word
@@ -144,7 +149,33 @@ lfp_status check_views(const lfp_view* views, int n_views) {
     return LFP_OK;
 }
 
-GridDev grid_dev(const lfp_grid* g) {
+// Skip levels of a valid descriptor, ascending: its own block side k = N / M
+// and those of k / 4, k / 2, 2 k that are whole numbers >= 2 with an even
+// number of blocks per side. Returns the count; ks has room for
+// LFP_MAX_SKIP_LEVELS.
+int skip_levels(const lfp_grid_desc& d, int* ks) {
+    const int k = d.N / d.M;
+    int n = 0;
+    const int cand[LFP_MAX_SKIP_LEVELS][2] = {{k, 4}, {k, 2}, {k, 1}, {2 * k, 1}};  // side = a / b
+    for (auto& c : cand) {
+        if (c[0] % c[1]) continue;
+        const int kk = c[0] / c[1];
+        if (kk != k && (kk < 2 || d.N % kk || ((d.N / kk) & 1))) continue;
+        ks[n++] = kk;
+    }
+    return n;
+}
+
+// the skip level whose block side is k, or -1
+int skip_level_of(const lfp_grid* g, int k) {
+    for (int l = 0; l < g->n_skip; ++l)
+        if (g->skip_k[l] == k) return l;
+    return -1;
+}
+
+// level: index into g->skip_k, or -1 for the grid's default
+GridDev grid_dev(const lfp_grid* g, int level = -1) {
+    if (level < 0) level = g->skip;
     GridDev d;
     const lfp_grid_desc& s = g->desc;
     d.nx = s.nx;
@@ -155,8 +186,8 @@ GridDev grid_dev(const lfp_grid* g) {
     d.oz = s.origin[2];
     d.spacing = s.spacing;
     d.N = s.N;
-    d.M = s.M;
-    d.k = s.N / s.M;
+    d.k = g->skip_k[level];
+    d.M = s.N / d.k;
     d.kinv = (unsigned)(((1ull << 31) + (unsigned long long)d.k - 1) / (unsigned long long)d.k);
     d.two_way = s.thickness_rel < 0.0f ? 1 : 0;
     d.kappa = (float)(1.0 + 4.0 * (double)std::max(s.thickness_rel, 0.0f) / s.N);
@@ -165,7 +196,7 @@ GridDev grid_dev(const lfp_grid* g) {
     d.eye_nearest = s.eye_lookup == LFP_EYE_NEAREST ? 1 : 0;
     d.nearest_probes = s.traversal == LFP_TRAVERSAL_NEAREST ? 1 : 0;
     d.dist = g->dist;
-    d.mip = g->mip;
+    d.mip = g->skip_mip[level];
     d.nrm = g->nrm;
     d.rad = g->rad;
     d.flags = g->flags;
@@ -205,7 +236,12 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
     const bool overlapped = queue != nullptr;
     if (!queue) queue = g->tile_counter;  // the persistent launches' work-queue head
     int tw = g->tile_w, th = g->tile_h, sched = g->schedule, flat = 0, engine = g->engine, occ = g->stream_occ;
+    int level = g->skip;
     if (opts) {
+        if (opts->skip_block) {
+            level = skip_level_of(g, opts->skip_block);
+            if (level < 0) return LFP_ERR_INVALID_ARG;
+        }
         if (opts->engine < LFP_ENGINE_AUTO || opts->engine > LFP_ENGINE_NESTED) return LFP_ERR_INVALID_ARG;
         if (opts->engine != LFP_ENGINE_AUTO) engine = opts->engine;
         if (opts->occupancy < LFP_OCC_AUTO || opts->occupancy > LFP_OCC_9) return LFP_ERR_INVALID_ARG;
@@ -222,7 +258,7 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
     }
     for (unsigned char u : g->uploaded)
         if (!u) return LFP_ERR_STATE;
-    GridDev gd = grid_dev(g);
+    GridDev gd = grid_dev(g, level);
     static thread_local ViewBatch vb;  // ~10 KB: keep it off the host stack
     // the streaming engine runs the hierarchical march (both traversals); the
     // flat march runs on the loop nest
@@ -284,7 +320,7 @@ void destroy(lfp_grid* g) {
     DeviceGuard dg(g->device);
     cudaDeviceSynchronize();
     dev_free(g->dist);
-    dev_free(g->mip);
+    for (float* m : g->skip_mip) dev_free(m);
     dev_free(g->nrm);
     dev_free(g->rad);
     dev_free(g->flags);
@@ -324,6 +360,8 @@ bool grid_access(const lfp_grid* g, GridAccess* out) {
     return true;
 }
 
+bool grid_has_skip(const lfp_grid* g, int k) { return g && skip_level_of(g, k) >= 0; }
+
 ViewDev view_dev_of(const lfp_view& v, int tile_w, int tile_h, int tile_begin) {
     return view_dev(v, tile_w, tile_h, tile_begin);
 }
@@ -349,6 +387,18 @@ lfp_status ensure(T** buf, size_t* have, size_t need, cudaStream_t s) {
     return LFP_OK;
 }
 
+// the min/max maps of probes [first, first + count) at every skip level
+cudaError_t build_skip_maps(lfp_grid* g, int first, int count, cudaStream_t s) {
+    const int N = g->desc.N;
+    const float* dist = g->dist + (size_t)first * N * N;
+    for (int l = 0; l < g->n_skip; ++l) {
+        const int M = N / g->skip_k[l];
+        cudaError_t e = launch_build_mip(dist, g->skip_mip[l] + (size_t)first * 2 * M * M, count, N, M, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -371,8 +421,18 @@ lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes) 
     LFP_TRY(check_desc(desc));
     if (!bytes) return LFP_ERR_INVALID_ARG;
     unsigned long long P = (unsigned long long)desc->nx * desc->ny * desc->nz;
-    unsigned long long NN = (unsigned long long)desc->N * desc->N, MM = (unsigned long long)desc->M * desc->M;
+    unsigned long long NN = (unsigned long long)desc->N * desc->N, MM = 0;
+    int ks[LFP_MAX_SKIP_LEVELS];
+    const int n = skip_levels(*desc, ks);
+    for (int l = 0; l < n; ++l) MM += (unsigned long long)(desc->N / ks[l]) * (desc->N / ks[l]);
     *bytes = P * (NN * (4 + nrm_bytes(desc->normal_fmt) + rad_bytes(desc->radiance_fmt)) + MM * 8);
+    return LFP_OK;
+}
+
+lfp_status lfp_skip_blocks(const lfp_grid_desc* desc, int* blocks, int* count) {
+    LFP_TRY(check_desc(desc));
+    if (!blocks || !count) return LFP_ERR_INVALID_ARG;
+    *count = skip_levels(*desc, blocks);
     return LFP_OK;
 }
 
@@ -385,10 +445,15 @@ lfp_status lfp_create_grid(const lfp_grid_desc* desc, lfp_grid** out) {
     g->desc = *desc;
     g->P = desc->nx * desc->ny * desc->nz;
     g->uploaded.assign(g->P, 0);
-    size_t NN = (size_t)desc->N * desc->N, MM = (size_t)desc->M * desc->M;
+    size_t NN = (size_t)desc->N * desc->N;
     lfp_status st = LFP_OK;
     if (st == LFP_OK) st = dev_alloc((void**)&g->dist, g->P * NN * 4);
-    if (st == LFP_OK) st = dev_alloc((void**)&g->mip, g->P * MM * 8);
+    g->n_skip = skip_levels(*desc, g->skip_k);
+    for (int l = 0; l < g->n_skip; ++l) {
+        const size_t M = desc->N / g->skip_k[l];
+        if (g->skip_k[l] == desc->N / desc->M) g->skip = l;
+        if (st == LFP_OK) st = dev_alloc((void**)&g->skip_mip[l], g->P * M * M * 8);
+    }
     if (st == LFP_OK) st = dev_alloc(&g->nrm, g->P * NN * nrm_bytes(desc->normal_fmt));
     if (st == LFP_OK) st = dev_alloc(&g->rad, g->P * NN * rad_bytes(desc->radiance_fmt));
     if (st == LFP_OK) st = dev_alloc((void**)&g->flags, 2 * sizeof(unsigned));
@@ -446,7 +511,7 @@ lfp_status lfp_upload_probes(lfp_grid* g, int first_probe, int count, const lfp_
                                              g->desc.radiance_fmt, n, s));
         }
     }
-    LFP_CUDA(launch_build_mip(dist_dst, g->mip + (size_t)first_probe * 2 * g->desc.M * g->desc.M, count, N, g->desc.M, s));
+    LFP_CUDA(build_skip_maps(g, first_probe, count, s));
     for (int p = first_probe; p < first_probe + count; ++p) g->uploaded[p] = 1;
     return LFP_OK;
 }
@@ -500,10 +565,7 @@ lfp_status lfp_build_probes_from_points(lfp_grid* g, int first_probe, int count,
                                         g->desc.radiance_fmt, m, s);
         if (e != cudaSuccess) st = LFP_ERR_CUDA;
     }
-    if (st == LFP_OK &&
-        launch_build_mip(g->dist + (size_t)first_probe * NN, g->mip + (size_t)first_probe * 2 * g->desc.M * g->desc.M,
-                         count, N, g->desc.M, s) != cudaSuccess)
-        st = LFP_ERR_CUDA;
+    if (st == LFP_OK && build_skip_maps(g, first_probe, count, s) != cudaSuccess) st = LFP_ERR_CUDA;
     if (st == LFP_OK)
         for (int p = first_probe; p < first_probe + count; ++p) g->uploaded[p] = 1;
     return st;
@@ -571,13 +633,61 @@ lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const l
     out.aux_uv = o->aux_uv;
     out.hit_texel = nullptr;
     out.counters = nullptr;
+    cudaEvent_t e0, e1;
+    LFP_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return LFP_ERR_CUDA;
+    }
+    // Each candidate: one timed warm-up launch; a candidate whose warm-up
+    // took more than twice the best per-launch time so far is dropped, the
+    // others get one more warm-up and three timed launches.
+    lfp_status st = LFP_OK;
+    auto timed = [&](const lfp_render_opts& k, int reps, float* ms) -> lfp_status {
+        if (cudaEventRecord(e0, s) != cudaSuccess) return LFP_ERR_CUDA;
+        for (int r = 0; r < reps; ++r) LFP_TRY(render_impl(g, views, n_views, out, &k, s));
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+            return LFP_ERR_CUDA;
+        return LFP_OK;
+    };
+    auto fastest = [&](const std::vector<lfp_render_opts>& cand, lfp_render_opts* pick) -> lfp_status {
+        float best_ms = 3.4e38f;
+        *pick = cand[0];
+        for (const lfp_render_opts& k : cand) {
+            float ms = 0.f;
+            LFP_TRY(timed(k, 1, &ms));
+            if (ms > 2.0f * best_ms) continue;  // clearly slower: pruned
+            LFP_TRY(render_impl(g, views, n_views, out, &k, s));
+            LFP_TRY(timed(k, 3, &ms));
+            if (ms / 3.0f < best_ms) {
+                best_ms = ms / 3.0f;
+                *pick = k;
+            }
+        }
+        return LFP_OK;
+    };
     std::vector<lfp_render_opts> cand;
-    lfp_render_opts c;
-    std::memset(&c, 0, sizeof(c));
+    lfp_render_opts c, pick;
+    // 1. the skip level, on the streaming engine with the 8-block budget
+    for (int l = 0; l < g->n_skip; ++l) {
+        std::memset(&c, 0, sizeof(c));
+        c.engine = LFP_ENGINE_STREAM;
+        c.occupancy = LFP_OCC_8;
+        c.skip_block = g->skip_k[l];
+        cand.push_back(c);
+    }
+    st = fastest(cand, &pick);
+    const int skip_block = pick.skip_block;
+    // 2. the launch configuration at that level (the streaming candidates
+    // come first and usually set the time that prunes the loop nest's)
+    cand.clear();
     for (int oc : {LFP_OCC_8, LFP_OCC_9})
         if (oc == LFP_OCC_8 || g->desc.traversal == LFP_TRAVERSAL_GRID) {
+            std::memset(&c, 0, sizeof(c));
             c.engine = LFP_ENGINE_STREAM;
             c.occupancy = oc;
+            c.skip_block = skip_block;
             cand.push_back(c);
         }
     const int shapes[5][2] = {{8, 4}, {8, 8}, {16, 8}, {16, 16}, {32, 8}};
@@ -588,46 +698,15 @@ lfp_status lfp_autotune(lfp_grid* g, const lfp_view* views, int n_views, const l
             c.tile_w = sh[0];
             c.tile_h = sh[1];
             c.schedule = sched;
+            c.skip_block = skip_block;
             cand.push_back(c);
         }
-    cudaEvent_t e0, e1;
-    LFP_CUDA(cudaEventCreate(&e0));
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return LFP_ERR_CUDA;
-    }
-    // Each candidate: one timed warm-up launch; a candidate whose warm-up
-    // took more than twice the best per-launch time so far is dropped (the
-    // streaming candidates come first and usually set that time), the others
-    // get one more warm-up and three timed launches.
-    lfp_status st = LFP_OK;
-    float best_ms = 3.4e38f;
-    lfp_render_opts pick = cand[0];
-    auto timed = [&](const lfp_render_opts& k, int reps, float* ms) -> lfp_status {
-        if (cudaEventRecord(e0, s) != cudaSuccess) return LFP_ERR_CUDA;
-        for (int r = 0; r < reps; ++r) LFP_TRY(render_impl(g, views, n_views, out, &k, s));
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
-            return LFP_ERR_CUDA;
-        return LFP_OK;
-    };
-    for (const lfp_render_opts& k : cand) {
-        float ms = 0.f;
-        st = timed(k, 1, &ms);
-        if (st != LFP_OK) break;
-        if (ms > 2.0f * best_ms) continue;  // clearly slower: pruned
-        st = render_impl(g, views, n_views, out, &k, s);
-        if (st == LFP_OK) st = timed(k, 3, &ms);
-        if (st != LFP_OK) break;
-        if (ms / 3.0f < best_ms) {
-            best_ms = ms / 3.0f;
-            pick = k;
-        }
-    }
+    if (st == LFP_OK) st = fastest(cand, &pick);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LFP_OK) return st;
     g->engine = pick.engine;
+    g->skip = skip_level_of(g, pick.skip_block);
     if (pick.engine == LFP_ENGINE_STREAM) g->stream_occ = pick.occupancy == LFP_OCC_9 ? 1 : 0;
     if (pick.engine == LFP_ENGINE_NESTED) {
         g->tile_w = pick.tile_w;
@@ -645,6 +724,9 @@ lfp_status lfp_set_defaults(lfp_grid* g, const lfp_render_opts* o) {
     if (o->schedule < LFP_SCHED_AUTO || o->schedule > LFP_SCHED_PERSISTENT) return LFP_ERR_INVALID_ARG;
     if ((o->tile_w || o->tile_h) && !valid_tile(o->tile_w, o->tile_h)) return LFP_ERR_INVALID_ARG;
     if (o->march != LFP_MARCH_HIER) return LFP_ERR_INVALID_ARG;  // the flat march is a per-call diagnostic
+    const int level = o->skip_block ? skip_level_of(g, o->skip_block) : g->skip;
+    if (level < 0) return LFP_ERR_INVALID_ARG;
+    g->skip = level;
     if (o->engine != LFP_ENGINE_AUTO) g->engine = o->engine;
     if (o->occupancy != LFP_OCC_AUTO) g->stream_occ = o->occupancy == LFP_OCC_9 ? 1 : 0;
     if (o->tile_w) {

@@ -82,6 +82,10 @@ extern "C" lfp_status lfp_render_levels(lfp_grid* const* levels, int n_levels, c
     if (!out) return LFP_ERR_INVALID_ARG;
     std::vector<std::vector<lfp_view>> by_level;
     lfp_status st = group(levels, n_levels, views, n_views, by_level);
+    // a skip level given in opts must exist on every level that renders
+    for (int k = 0; k < n_levels && st == LFP_OK; ++k)
+        if (opts && opts->skip_block && !by_level[k].empty() && !lfp::grid_has_skip(levels[k], opts->skip_block))
+            st = LFP_ERR_INVALID_ARG;
     for (int k = 0; k < n_levels && st == LFP_OK; ++k)
         if (!by_level[k].empty())
             st = lfp_render_ex(levels[k], by_level[k].data(), (int)by_level[k].size(), out, opts, stream);

@@ -65,6 +65,8 @@ struct GridAccess {
     int all_uploaded;
 };
 bool grid_access(const struct lfp_grid* g, GridAccess* out);
+// true if the grid keeps a skip level of block side k (lfp_skip_blocks)
+bool grid_has_skip(const struct lfp_grid* g, int k);
 // lfp_view -> kernel view constants (tile_w x tile_h ray tiles)
 ViewDev view_dev_of(const lfp_view& v, int tile_w, int tile_h, int tile_begin);
 // 0 if the views are valid (lfp_status otherwise)

@@ -29,6 +29,7 @@ LFP_OCC_AUTO, LFP_OCC_8, LFP_OCC_9 = 0, 1, 2
 LFP_EYE_BILINEAR, LFP_EYE_NEAREST = 0, 1
 LFP_TRAVERSAL_GRID, LFP_TRAVERSAL_NEAREST = 0, 1
 LFP_NEAREST_MAX_PROBES = 8
+LFP_MAX_SKIP_LEVELS = 4
 N_COUNTERS = 8
 COUNTER_NAMES = ("coarse", "fine", "normal", "radiance", "cells", "probes", "hits", "rays")
 
@@ -60,7 +61,8 @@ class lfp_outputs(ctypes.Structure):
 
 class lfp_render_opts(ctypes.Structure):
     _fields_ = [("march", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("engine", ctypes.c_int), ("occupancy", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("engine", ctypes.c_int), ("occupancy", ctypes.c_int),
+                ("skip_block", ctypes.c_int)]
 
 
 class lfp_point_cloud(ctypes.Structure):
@@ -100,6 +102,7 @@ def _load():
         "lfp_set_radiance": ([vp, vp, vp], i),
         "lfp_check_flags": ([vp, vp], i),
         "lfp_grid_bytes": ([P(lfp_grid_desc), P(ctypes.c_ulonglong)], i),
+        "lfp_skip_blocks": ([P(lfp_grid_desc), P(i), P(i)], i),
         "lfp_destroy_grid": ([vp], None),
         "lfp_status_string": ([i], ctypes.c_char_p),
     }
@@ -234,6 +237,14 @@ def lfp_grid_bytes(desc: lfp_grid_desc) -> int:
     b = ctypes.c_ulonglong()
     _check(_lib.lfp_grid_bytes(ctypes.byref(desc), ctypes.byref(b)), "lfp_grid_bytes")
     return b.value
+
+
+def lfp_skip_blocks(desc: lfp_grid_desc) -> list:
+    """The block sides of the grid's skip levels, ascending."""
+    ks = (ctypes.c_int * LFP_MAX_SKIP_LEVELS)()
+    n = ctypes.c_int()
+    _check(_lib.lfp_skip_blocks(ctypes.byref(desc), ks, ctypes.byref(n)), "lfp_skip_blocks")
+    return list(ks[:n.value])
 
 
 def raw_call(name: str, *args) -> int:

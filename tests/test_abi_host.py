@@ -102,12 +102,44 @@ def test_status_strings(lib):
 
 
 def test_grid_bytes_accounting(lib):
-    """Storage per probe: N^2 (4 distance + normal + radiance) + M^2 * 8 bytes;
-    FP16 texels halve the normal (8 -> 4) and radiance (16 -> 8) bytes."""
+    """Storage per probe: N^2 (4 distance + normal + radiance) bytes plus
+    8 bytes (min, max) per block of every skip level: N = 256 with blocks of
+    4, 8, 16 and 32 texels has 64^2 + 32^2 + 16^2 + 8^2 blocks. FP16 texels
+    halve the normal (8 -> 4) and radiance (16 -> 8) bytes."""
     d = _desc(lib, nx=4, ny=4, nz=4, N=256, M=16)
-    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 8 + 16) + 16 * 16 * 8)
+    blocks = 64 * 64 + 32 * 32 + 16 * 16 + 8 * 8
+    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 8 + 16) + blocks * 8)
     d.radiance_fmt = d.normal_fmt = lib.LFP_TEXEL_F16
-    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 4 + 8) + 16 * 16 * 8)
+    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 4 + 8) + blocks * 8)
+
+
+@pytest.mark.parametrize("N,M,want", [
+    (256, 16, [4, 8, 16, 32]),   # k = 16: k/4, k/2, k, 2k
+    (512, 32, [4, 8, 16, 32]),
+    (64, 16, [2, 4, 8]),         # k/4 = 1 is no skip
+    (48, 16, [3, 6]),            # k = 3: k/4, k/2 not whole
+    (192, 16, [3, 6, 12, 24]),
+    (6, 2, [3]),                 # 2k = 6 leaves one block per side (odd)
+    (256, 256, [1, 2]),          # the descriptor's own k = 1 is kept
+    (96, 2, [12, 24, 48]),       # 2k = 96 leaves one block per side
+    (40, 4, [5, 10, 20]),        # k = 10: k/4 not whole, k/2 = 5, 2k = 20 (two blocks per side)
+])
+def test_skip_levels_of_a_descriptor(lib, N, M, want):
+    """The skip levels: block sides k/4, k/2, 2k (k = N/M) that are whole,
+    >= 2, divide N into an even number of blocks, plus k itself."""
+    got = lib.lfp_skip_blocks(_desc(lib, N=N, M=M))
+    assert got == want
+    assert N // M in got
+    for k in got:
+        assert N % k == 0 and ((N // k) % 2 == 0 or k == N // M)
+
+
+def test_skip_levels_reject_invalid_arguments(lib):
+    b = (ctypes.c_int * lib.LFP_MAX_SKIP_LEVELS)()
+    n = ctypes.c_int()
+    assert lib.raw_call("lfp_skip_blocks", ctypes.byref(_desc(lib, M=3)), b, ctypes.byref(n)) == lib.LFP_ERR_INVALID_ARG
+    assert lib.raw_call("lfp_skip_blocks", None, b, ctypes.byref(n)) == lib.LFP_ERR_INVALID_ARG
+    assert lib.raw_call("lfp_skip_blocks", ctypes.byref(_desc(lib)), None, ctypes.byref(n)) == lib.LFP_ERR_INVALID_ARG
 
 
 def test_allocation_fault_injection_returns_oom_without_a_device(lib):
