@@ -28,6 +28,7 @@ struct lfp_grid {
     int skip_k[LFP_MAX_SKIP_LEVELS] = {};
     float* skip_mip[LFP_MAX_SKIP_LEVELS] = {};
     int skip = 0;                       // default skip level (lfp_autotune, lfp_set_defaults)
+    float* qmin = nullptr;              // [P][4] least distance per map quadrant
     void* nrm = nullptr;
     void* rad = nullptr;
     unsigned* flags = nullptr;          // device flag word
@@ -197,6 +198,7 @@ GridDev grid_dev(const lfp_grid* g, int level = -1) {
     d.nearest_probes = s.traversal == LFP_TRAVERSAL_NEAREST ? 1 : 0;
     d.dist = g->dist;
     d.mip = g->skip_mip[level];
+    d.qmin = g->qmin;
     d.nrm = g->nrm;
     d.rad = g->rad;
     d.flags = g->flags;
@@ -321,6 +323,7 @@ void destroy(lfp_grid* g) {
     cudaDeviceSynchronize();
     dev_free(g->dist);
     for (float* m : g->skip_mip) dev_free(m);
+    dev_free(g->qmin);
     dev_free(g->nrm);
     dev_free(g->rad);
     dev_free(g->flags);
@@ -396,7 +399,7 @@ cudaError_t build_skip_maps(lfp_grid* g, int first, int count, cudaStream_t s) {
         cudaError_t e = launch_build_mip(dist, g->skip_mip[l] + (size_t)first * 2 * M * M, count, N, M, s);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return launch_build_qmin(dist, g->qmin + (size_t)first * 4, count, N, s);
 }
 
 }  // namespace
@@ -425,7 +428,7 @@ lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes) 
     int ks[LFP_MAX_SKIP_LEVELS];
     const int n = skip_levels(*desc, ks);
     for (int l = 0; l < n; ++l) MM += (unsigned long long)(desc->N / ks[l]) * (desc->N / ks[l]);
-    *bytes = P * (NN * (4 + nrm_bytes(desc->normal_fmt) + rad_bytes(desc->radiance_fmt)) + MM * 8);
+    *bytes = P * (NN * (4 + nrm_bytes(desc->normal_fmt) + rad_bytes(desc->radiance_fmt)) + MM * 8 + 4 * 4);
     return LFP_OK;
 }
 
@@ -454,6 +457,7 @@ lfp_status lfp_create_grid(const lfp_grid_desc* desc, lfp_grid** out) {
         if (g->skip_k[l] == desc->N / desc->M) g->skip = l;
         if (st == LFP_OK) st = dev_alloc((void**)&g->skip_mip[l], g->P * M * M * 8);
     }
+    if (st == LFP_OK) st = dev_alloc((void**)&g->qmin, g->P * 4 * sizeof(float));
     if (st == LFP_OK) st = dev_alloc(&g->nrm, g->P * NN * nrm_bytes(desc->normal_fmt));
     if (st == LFP_OK) st = dev_alloc(&g->rad, g->P * NN * rad_bytes(desc->radiance_fmt));
     if (st == LFP_OK) st = dev_alloc((void**)&g->flags, 2 * sizeof(unsigned));

@@ -10,6 +10,8 @@
 //                                 is exact; the walk reads the min plane at
 //                                 every low-resolution visit and the max
 //                                 only at a candidate
+//   qmin [P][4]     f32           per quadrant of the map, its least distance
+//                                 (where a segment's low-resolution walk starts)
 //   nrm  [P][N][N]  float2|half2  surface normal, octahedral-encoded
 //   rad  [P][N][N]  float4|half4  radiance RGB (+ pad), 16 / 8 bytes, so the
 //                                 two texels of one bilinear row are one
@@ -39,6 +41,7 @@ struct GridDev {
     int nearest_probes;       // traversal for fewer than 8 probes (Sec. 4.3)
     const float* dist;
     const float* mip;         // [P][2][M][M]
+    const float* qmin;        // [P][4]: the least distance in each quadrant of the map
     const void* nrm;
     const void* rad;
     unsigned* flags;          // bit 0: step limit reached; bit 1: texel index out of range (checked builds)

@@ -36,6 +36,8 @@ cudaError_t launch_encode_normals(const float* xyz, void* nrm, int nrm_fmt, long
 cudaError_t launch_convert_radiance(const float* rgb, void* rad, int rad_fmt, long long n, cudaStream_t s);
 // per-block min/max of the distance maps for `count` probes, into [count][2][M][M]
 cudaError_t launch_build_mip(const float* dist, float* mip, int count, int N, int M, cudaStream_t s);
+// least distance per quadrant of each probe's map, into qmin [count][4]
+cudaError_t launch_build_qmin(const float* dist, float* qmin, int count, int N, cudaStream_t s);
 // adjoint scatter into grad_radiance [P][N][N][3]; reduction: 1 per-pixel
 // atomics, 2 warp-aggregated atomics, 3 block-local sort by texel. HIT
 // pixels whose saved probe index is outside [0, P) are skipped and set

@@ -242,7 +242,8 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
     CF(kK0) = s.k[0];
     CF(kK1) = s.k[1];
     CF(kUend) = s.u_end;
-    CI(kQuad) = (s.lo[0] > 0 ? 1 : 0) | (s.lo[1] > 0 ? 2 : 0);
+    const int quad = (s.lo[0] > 0 ? 1 : 0) | (s.lo[1] > 0 ? 2 : 0);
+    CI(kQuad) = quad;
     L.e = s.e;
     L.m0 = s.m[0];
     L.m1 = s.m[1];
@@ -259,19 +260,33 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
         L.probe = p;
         (void)unused;
     }
+    // the walk starts where the ray first reaches the least distance of the
+    // segment's map quadrant (segment_start; the nearest-probe traversal,
+    // whose segments gain less than the set-up costs, starts at u = 0)
+    float us = 0.0f;
+    if (!NEAREST) {
+        bool walk;
+        us = segment_start(s, __ldg(g.qmin + (size_t)L.probe * 4 + quad), walk);
+        if (!walk) {
+            L.mode = kSegEnd;
+            return;
+        }
+    }
+    L.mode = kWalk;
     L.plane = g.mip + (size_t)L.probe * 2 * g.M * g.M;
     const int k = g.k, N = g.N;
     L.level = 0;
     coarse_box(g, L);
     const int hm1 = g.M / 2 - 1;
-    L.i = min(max(div_k(g.kinv, texel_of(s.p0[0], N, L.dir0)), L.lo0), L.lo0 + hm1);
-    L.j = min(max(div_k(g.kinv, texel_of(s.p0[1], N, L.dir1)), L.lo1), L.lo1 + hm1);
-    L.u = 0.0f;
+    L.i = min(max(div_k(g.kinv, texel_of(fmaf(s.k[0], us, s.p0[0]), N, L.dir0)), L.lo0), L.lo0 + hm1);
+    L.j = min(max(div_k(g.kinv, texel_of(fmaf(s.k[1], us, s.p0[1]), N, L.dir1)), L.lo1), L.lo1 + hm1);
+    L.u = us;
     L.u1 = s.u_end;
-    L.Pa = L.A0;
-    L.D2a = 1.0f;
-    L.ux = L.dir0 == 0 ? kInf : fmaxf(fmaf((float)((L.dir0 > 0 ? L.i + 1 : L.i) * k), L.m0, L.q0), 0.0f);
-    L.uy = L.dir1 == 0 ? kInf : fmaxf(fmaf((float)((L.dir1 > 0 ? L.j + 1 : L.j) * k), L.m1, L.q1), 0.0f);
+    const float Ds = fmaf(-L.e, us, 1.0f);
+    L.Pa = fmaf(fmaf(L.A2, us, L.A1), us, L.A0);
+    L.D2a = Ds * Ds;
+    L.ux = L.dir0 == 0 ? kInf : fmaxf(fmaf((float)((L.dir0 > 0 ? L.i + 1 : L.i) * k), L.m0, L.q0), us);
+    L.uy = L.dir1 == 0 ? kInf : fmaxf(fmaf((float)((L.dir1 > 0 ? L.j + 1 : L.j) * k), L.m1, L.q1), us);
 }
 
 // tau from the segment start of walk parameter u (infinite past the end),
@@ -680,10 +695,7 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
             probe_start<NEAREST>(g, L);
             L.mode = kSegStart;
         }
-        if (L.mode == kSegStart) {
-            seg_start<NEAREST>(g, L);
-            L.mode = kWalk;
-        }
+        if (L.mode == kSegStart) seg_start<NEAREST>(g, L);  // kWalk, or kSegEnd for a segment nearer than its quadrant
 
         // ---- walk phase: one texel visit per walking lane per step, until
         // kBatchPct % of the busy lanes wait for a transition ----

@@ -198,6 +198,29 @@ __device__ __forceinline__ float fine_start(const Seg& s, float d2, float u0, fl
     return fminf(fmaxf(us, u0), u1);
 }
 
+// Where a segment's low-resolution walk can start (grid traversal). dq is
+// the least distance stored in the segment's quadrant of the map: while the
+// ray's radial distance stays below dq it is in front of every texel there,
+// so the walk starts where it first reaches dq (the fine_start estimate over
+// the whole segment, never past that point). f(u) = A(u) - dq^2 D(u)^2 is
+// |Ya + tau w|^2 - dq^2 up to a positive factor, convex in tau: negative at
+// both ends means negative throughout, and `walk` is false (the segment is a
+// MISS without a visit). Returns 0 when the ray starts at or beyond dq.
+__device__ __forceinline__ float segment_start(const Seg& s, float dq, bool& walk) {
+    walk = true;
+    const float d2q = dq * dq;
+    const float f0 = fmaf(-d2q, 1.0f, s.A0);
+    if (!(f0 < 0.0f)) return 0.0f;
+    const float ue = s.u_end;
+    const float De = fmaf(-s.e, ue, 1.0f);
+    const float f1 = fmaf(-d2q, De * De, fmaf(fmaf(s.A2, ue, s.A1), ue, s.A0));
+    if (!(f1 >= 0.0f)) {
+        walk = false;
+        return 0.0f;
+    }
+    return fine_start(s, d2q, 0.0f, f0, ue, f1);
+}
+
 // highResolutionTracing over full-resolution texels inside the index box
 // [lo, hi] for u in [u0, u1]. P0, D20: |Ya + u0 V|^2 and (1 - e u0)^2.
 // Returns true when a decision was reached.
@@ -272,14 +295,22 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
         return fine_walk<NRMF, COUNT>(g, s, pbase, 0.0f, s.u_end, s.A0, 1.0f, s.lo[0], s.lo[1], s.hi[0], s.hi[1],
                                       out, st, step_limited);
     const float* mip = g.mip + (size_t)probe * 2 * M * M;  // min plane; the max plane follows it
+    float u = 0.0f;
+    if (!g.nearest_probes) {
+        bool walk;
+        const int quad = (s.lo[0] > 0 ? 1 : 0) | (s.lo[1] > 0 ? 2 : 0);
+        u = segment_start(s, __ldg(g.qmin + (size_t)probe * 4 + quad), walk);
+        if (!walk) return false;
+    }
     int clo0 = div_k(g.kinv, s.lo[0]), chi0 = div_k(g.kinv, s.hi[0]);
     int clo1 = div_k(g.kinv, s.lo[1]), chi1 = div_k(g.kinv, s.hi[1]);
-    int I = min(max(div_k(g.kinv, texel_of(s.p0[0], N, s.dir[0])), clo0), chi0);
-    int J = min(max(div_k(g.kinv, texel_of(s.p0[1], N, s.dir[1])), clo1), chi1);
+    int I = min(max(div_k(g.kinv, texel_of(fmaf(s.k[0], u, s.p0[0]), N, s.dir[0])), clo0), chi0);
+    int J = min(max(div_k(g.kinv, texel_of(fmaf(s.k[1], u, s.p0[1]), N, s.dir[1])), clo1), chi1);
     // coarse boundaries are full-resolution boundaries b = I k: same crossings
-    float ux = s.dir[0] == 0 ? kInf : fmaxf(fmaf((float)((s.dir[0] > 0 ? I + 1 : I) * k), s.m[0], s.q[0]), 0.0f);
-    float uy = s.dir[1] == 0 ? kInf : fmaxf(fmaf((float)((s.dir[1] > 0 ? J + 1 : J) * k), s.m[1], s.q[1]), 0.0f);
-    float u = 0.0f, Pa = s.A0, D2a = 1.0f;
+    float ux = s.dir[0] == 0 ? kInf : fmaxf(fmaf((float)((s.dir[0] > 0 ? I + 1 : I) * k), s.m[0], s.q[0]), u);
+    float uy = s.dir[1] == 0 ? kInf : fmaxf(fmaf((float)((s.dir[1] > 0 ? J + 1 : J) * k), s.m[1], s.q[1]), u);
+    const float Du = fmaf(-s.e, u, 1.0f);
+    float Pa = fmaf(fmaf(s.A2, u, s.A1), u, s.A0), D2a = Du * Du;
     const float u1 = s.u_end;
     for (int guard = 0; guard < 4 * M + 8; ++guard) {
         float un = fminf(ux, uy);
@@ -496,6 +527,7 @@ __device__ __forceinline__ float3 shade(const GridDev& g, int probe, float u, fl
     float w[4];
     bilinear_taps(g.N, u, v, idx, w);
     int pc = probe, zero = 0;
+    (void)zero;  // the index checks of checked builds redirect through it
     LFP_CHECK_TEXEL(g.flags, (unsigned)pc < (unsigned)(g.nx * g.ny * g.nz), pc, zero);
     size_t base = (size_t)pc * g.N * g.N;
     float3 c = make_float3(0.f, 0.f, 0.f);

@@ -66,6 +66,23 @@ __global__ void build_mip_kernel(const float* __restrict__ dist, float* __restri
     }
 }
 
+// Least distance of each quadrant of each probe's map: one block per
+// (probe, quadrant).
+__global__ void build_qmin_kernel(const float* __restrict__ dist, float* __restrict__ qmin, int N) {
+    const int p = blockIdx.x >> 2, q = blockIdx.x & 3, h = N / 2;
+    const float* base = dist + (size_t)p * N * N + (size_t)((q & 2) ? h : 0) * N + ((q & 1) ? h : 0);
+    float lo = __int_as_float(0x7f800000);
+    for (int t = threadIdx.x; t < h * h; t += blockDim.x) lo = fminf(lo, base[(size_t)(t / h) * N + t % h]);
+    for (int off = 16; off > 0; off >>= 1) lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+    __shared__ float part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) lo = fminf(lo, part[w]);
+        qmin[blockIdx.x] = fminf(lo, part[0]);
+    }
+}
+
 // Adjoint: for every HIT pixel add w_k * g_c into the 4 bilinear taps.
 __global__ void backward_kernel(int N, int P, unsigned* flags, PixBatch pb, const float* __restrict__ grad_rgb,
                                 const uint8_t* __restrict__ cls, const int32_t* __restrict__ aux_probe,
@@ -304,6 +321,11 @@ cudaError_t launch_convert_radiance(const float* rgb, void* rad, int rad_fmt, lo
 cudaError_t launch_build_mip(const float* dist, float* mip, int count, int N, int M, cudaStream_t s) {
     long long total = (long long)count * M * M;
     build_mip_kernel<<<blocks_for(total), kThreads, 0, s>>>(dist, mip, count, N, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_qmin(const float* dist, float* qmin, int count, int N, cudaStream_t s) {
+    build_qmin_kernel<<<count * 4, 256, 0, s>>>(dist, qmin, N);
     return cudaGetLastError();
 }
 

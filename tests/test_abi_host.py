@@ -102,15 +102,16 @@ def test_status_strings(lib):
 
 
 def test_grid_bytes_accounting(lib):
-    """Storage per probe: N^2 (4 distance + normal + radiance) bytes plus
-    8 bytes (min, max) per block of every skip level: N = 256 with blocks of
-    4, 8, 16 and 32 texels has 64^2 + 32^2 + 16^2 + 8^2 blocks. FP16 texels
-    halve the normal (8 -> 4) and radiance (16 -> 8) bytes."""
+    """Storage per probe: N^2 (4 distance + normal + radiance) bytes, 8
+    bytes (min, max) per block of every skip level (N = 256 with blocks of
+    4, 8, 16 and 32 texels has 64^2 + 32^2 + 16^2 + 8^2 blocks) and 16 bytes
+    for the least distance of each map quadrant. FP16 texels halve the
+    normal (8 -> 4) and radiance (16 -> 8) bytes."""
     d = _desc(lib, nx=4, ny=4, nz=4, N=256, M=16)
     blocks = 64 * 64 + 32 * 32 + 16 * 16 + 8 * 8
-    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 8 + 16) + blocks * 8)
+    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 8 + 16) + blocks * 8 + 16)
     d.radiance_fmt = d.normal_fmt = lib.LFP_TEXEL_F16
-    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 4 + 8) + blocks * 8)
+    assert lib.lfp_grid_bytes(d) == 64 * (256 * 256 * (4 + 4 + 8) + blocks * 8 + 16)
 
 
 @pytest.mark.parametrize("N,M,want", [

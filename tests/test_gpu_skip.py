@@ -133,3 +133,22 @@ def test_hierarchy_refuses_a_skip_level_missing_on_a_level():
     torch.cuda.synchronize()
     want = grids[level].render(views, aux=False, skip_block=opts.skip_block)
     assert torch.equal(cls, want["cls"]) and torch.equal(rgb, want["rgb"])
+
+
+@pytest.mark.parametrize("name", ["tiny", "room"])
+def test_flat_march_matches_every_skip_level(name):
+    """Appendix A's flat march (full-resolution map only, no skipping)
+    against the hierarchical walk at every skip level, with each segment's
+    walk started where the ray reaches its quadrant's least distance: the
+    skips pass only texels the ray is in front of, so the decisions agree
+    up to near-ties."""
+    import paper_2507_14624_gb300 as lfpk
+    sc, views, d, n, r = load_workload(name)
+    grid = lfpk.ProbeGrid(sc.grid)
+    grid.upload(d, n, r)
+    flat = grid.render(views, hit_texel=True, march=lfpk.LFP_MARCH_FLAT)
+    for k in grid.skip_blocks:
+        for eng in (lfpk.LFP_ENGINE_STREAM, lfpk.LFP_ENGINE_NESTED):
+            a = grid.render(views, hit_texel=True, skip_block=k, engine=eng)
+            same = (a["cls"] == flat["cls"]) & (a["texel"] == flat["texel"])
+            assert same.float().mean().item() >= 0.9999, (k, eng)
