@@ -36,6 +36,10 @@ constexpr int kStreamThreads = kStreamThreadsPerBlock;
 constexpr int kWalkSteps = LFP_STREAM_WALK_STEPS;  // most texel visits per lane between control rounds
 constexpr int kBatchPct = LFP_STREAM_BATCH_PCT;     // transitions run once this % of busy lanes wait
 constexpr unsigned kFull = 0xffffffffu;
+#ifndef LFP_STREAM_CHAIN_PASSES
+#define LFP_STREAM_CHAIN_PASSES 8
+#endif
+constexpr int kChainPasses = LFP_STREAM_CHAIN_PASSES;  // transition passes per control round
 
 enum Mode : int {
     kIdle = 0,     // no ray: take one from the pool
@@ -642,60 +646,68 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
         if (exhausted && L.mode == kIdle) L.mode = kExit;
         if (__all_sync(kFull, L.mode == kExit)) break;
 
-        if (L.mode == kSegEnd) {  // MISS on this segment: next segment, or the probe is a MISS
-            if (CI(kSegFinal)) {
-                if (NEAREST) {  // a MISS falls through to the next probe too
-                    const int q = CI(kQ) + 1;
-                    CI(kQ) = q;
-                    L.mode = q == n_probes ? kNextCell : kProbeStart;
+        // the transitions run again while a lane's new segment ended at its
+        // set-up (nearer than its quadrant's least distance), so such lanes
+        // reach their next segment in the same round (one pass for the
+        // nearest-probe traversal, whose segments always walk)
+#pragma unroll 1
+        for (int pass = 0; pass < (NEAREST ? 1 : kChainPasses); ++pass) {
+            if (L.mode == kSegEnd) {  // MISS on this segment: next segment, or the probe is a MISS
+                if (CI(kSegFinal)) {
+                    if (NEAREST) {  // a MISS falls through to the next probe too
+                        const int q = CI(kQ) + 1;
+                        CI(kQ) = q;
+                        L.mode = q == n_probes ? kNextCell : kProbeStart;
+                    } else {
+                        L.mode = kNextCell;
+                    }
                 } else {
-                    L.mode = kNextCell;
+                    CI(kSegI) += 1;
+                    CF(kSegA) = CF(kSegB);
+                    L.mode = kSegStart;
                 }
-            } else {
-                CI(kSegI) += 1;
-                CF(kSegA) = CF(kSegB);
-                L.mode = kSegStart;
             }
-        }
-        if (L.mode == kUnknownRes) {  // UNKNOWN falls through to the next probe of the cage
-            const int q = CI(kQ) + 1;
-            CI(kQ) = q;
-            if (NEAREST) {  // any UNKNOWN makes an undecided ray UNKNOWN
-                CI(kCbits) |= 0x200;
-                L.mode = q == n_probes ? kNextCell : kProbeStart;
-            } else if (q == 8) {
-                CI(kCbits) |= 0x200;  // saw UNKNOWN
-                L.mode = kNextCell;
-            } else {
+            if (L.mode == kUnknownRes) {  // UNKNOWN falls through to the next probe of the cage
+                const int q = CI(kQ) + 1;
+                CI(kQ) = q;
+                if (NEAREST) {  // any UNKNOWN makes an undecided ray UNKNOWN
+                    CI(kCbits) |= 0x200;
+                    L.mode = q == n_probes ? kNextCell : kProbeStart;
+                } else if (q == 8) {
+                    CI(kCbits) |= 0x200;  // saw UNKNOWN
+                    L.mode = kNextCell;
+                } else {
+                    L.mode = kProbeStart;
+                }
+            }
+            if (L.mode == kNextCell) {
+                const int cbits = CI(kCbits);
+                if (cbits & 0x100) {  // last cell
+                    CI(kCls) = (cbits & 0x200) ? kUnknown : kMiss;
+                    L.mode = kRayDone;  // written at the next control round
+                } else {
+                    int ax = (cbits >> 6) & 3;
+                    int st_ax = step_of(cbits, ax);
+                    if (ax == 0) CI(kC0) += st_ax;
+                    else if (ax == 1) CI(kC1) += st_ax;
+                    else CI(kC2) += st_ax;
+                    CF(kTin) = CF(kTout);
+                    L.mode = kCellStart;
+                }
+            }
+            if (L.mode == kCellStart) {
+                ++cells;
+                cell_start(g);
                 L.mode = kProbeStart;
             }
-        }
-        if (L.mode == kNextCell) {
-            const int cbits = CI(kCbits);
-            if (cbits & 0x100) {  // last cell
-                CI(kCls) = (cbits & 0x200) ? kUnknown : kMiss;
-                L.mode = kRayDone;  // written at the next control round
-            } else {
-                int ax = (cbits >> 6) & 3;
-                int st_ax = step_of(cbits, ax);
-                if (ax == 0) CI(kC0) += st_ax;
-                else if (ax == 1) CI(kC1) += st_ax;
-                else CI(kC2) += st_ax;
-                CF(kTin) = CF(kTout);
-                L.mode = kCellStart;
+            if (L.mode == kProbeStart) {
+                ++probes;
+                probe_start<NEAREST>(g, L);
+                L.mode = kSegStart;
             }
+            if (L.mode == kSegStart) seg_start<NEAREST>(g, L);  // kWalk, or kSegEnd for a segment nearer than its quadrant
+            if (NEAREST || !__any_sync(kFull, L.mode == kSegEnd)) break;
         }
-        if (L.mode == kCellStart) {
-            ++cells;
-            cell_start(g);
-            L.mode = kProbeStart;
-        }
-        if (L.mode == kProbeStart) {
-            ++probes;
-            probe_start<NEAREST>(g, L);
-            L.mode = kSegStart;
-        }
-        if (L.mode == kSegStart) seg_start<NEAREST>(g, L);  // kWalk, or kSegEnd for a segment nearer than its quadrant
 
         // ---- walk phase: one texel visit per walking lane per step, until
         // kBatchPct % of the busy lanes wait for a transition ----
