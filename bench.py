@@ -71,6 +71,9 @@ def parse():
                     help="the autotuner's launch configuration (default), or the streaming engine pinned to 8 "
                          "blocks per SM (64 registers) or 9 (56 registers); the pinned forms are what the "
                          "per-kernel ncu counts are taken on")
+    ap.add_argument("--engine", default="auto", choices=["auto", "nested"],
+                    help="multiscale: the autotuner's launch configuration (default), or every level pinned to the "
+                         "loop-nest engine with 8x4 persistent ray tiles (the form its ncu counts are taken on)")
     ap.add_argument("--skip-block", default="auto",
                     help="the autotuner's skip level (default), or the block side of the min/max map the walk "
                          "skips with (one of the grid's skip levels; multiscale: one per level, comma-separated)")
@@ -666,12 +669,17 @@ def run_multiscale(args):
     pin_engine, pin_occ = 0, 0  # 0: each level's default (autotuned)
     if args.occupancy != "auto":
         pin_engine, pin_occ = lfpk.LFP_ENGINE_STREAM, OCCUPANCY[args.occupancy]
+    pinned = args.occupancy != "auto" or args.engine != "auto"
     pins = [0] * len(h.grids) if args.skip_block == "auto" else [int(x) for x in args.skip_block.split(",")]
     skips = []
     for k, g in enumerate(h.grids):  # each level's launch configuration from the autotuner
         mine = [v for v, l in zip(views, lev) if l == k]
-        if mine and args.occupancy == "auto":
+        if mine and not pinned:
             tuned[str(k)] = g.autotune(mine)
+        if args.engine == "nested":  # every level on the loop nest, 8x4 persistent tiles
+            o = lfp.lfp_render_opts()
+            o.engine, o.tile_w, o.tile_h, o.schedule = lfpk.LFP_ENGINE_NESTED, 8, 4, lfpk.LFP_SCHED_PERSISTENT
+            lfp.lfp_set_defaults(g.handle, o)
         if pins[k]:  # a pinned skip level becomes the level's default
             o = lfp.lfp_render_opts()
             o.skip_block = pins[k]
@@ -755,15 +763,21 @@ def run_multiscale(args):
 
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
-    # ncu counts were taken per level and register budget on a 9-view run of
-    # the same levels (per ray, scaled to this step's rays of each level, with
-    # the budget each level ran with); per launch = per step / launches
+    # ncu counts were taken per level on a 9-view run of the same levels, for
+    # each register budget of the streaming engine and for the loop nest with
+    # 8x4 persistent tiles (per ray, scaled to this step's rays of each level,
+    # with the configuration each level ran with); per launch = per step /
+    # launches
     summ = ncu_summary("multiscale", skip=skips).get("levels", {})
     kernels, inst, dram = {}, 0.0, 0.0
     for k in sorted(set(lev)):
         rays_k = sum(v.W * v.H for v, l in zip(views, lev) if l == k)
-        occ_k = occupancy_key(args.occupancy, tuned.get(str(k)))
-        kernels[str(k)] = f"render_stream_kernel ({occ_k} blocks/SM)" if occ_k else "render_kernel (loop nest)"
+        occ_k = "nested" if args.engine == "nested" else occupancy_key(args.occupancy, tuned.get(str(k)))
+        if occ_k is None and tuned.get(str(k), {}).get("tile") in ((8, 4), [8, 4]) and \
+                tuned[str(k)].get("schedule") == 2:  # LFP_SCHED_PERSISTENT
+            occ_k = "nested"
+        kernels[str(k)] = (f"render_stream_kernel ({occ_k} blocks/SM)" if occ_k not in (None, "nested") else
+                           "render_kernel (loop nest)")
         c = summ.get(str(k), {}).get("by_occupancy", {}).get(occ_k or "", {})
         if inst is not None and "warp_inst_per_ray" in c:
             inst += c["warp_inst_per_ray"] * rays_k
