@@ -28,7 +28,7 @@ using namespace trace;
 #define LFP_STREAM_WALK_STEPS 64
 #endif
 #ifndef LFP_STREAM_BATCH_PCT
-#define LFP_STREAM_BATCH_PCT 75
+#define LFP_STREAM_BATCH_PCT 80
 #endif
 // resident blocks per SM of the two register budgets (64 and 56 registers)
 constexpr int kMinBlocks[2] = {8, 9};
