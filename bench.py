@@ -197,6 +197,19 @@ def occupancy_key(pinned, tuned):
     return "9" if tuned.get("occupancy") == 2 else "8"  # LFP_OCC_9
 
 
+def level_config_key(engine_pin, occ_pin, tuned):
+    """The entry of a multi-scale level's count a launch may use: "8" / "9"
+    for the streaming engine's register budgets, "nested" for the loop nest
+    with 8x4 persistent tiles (the configuration its counts are taken on);
+    None for any other loop-nest configuration."""
+    if engine_pin == "nested":
+        return "nested"
+    key = occupancy_key(occ_pin, tuned)
+    if key is None and tuned and tuple(tuned.get("tile", ())) == (8, 4) and tuned.get("schedule") == 2:
+        return "nested"  # LFP_SCHED_PERSISTENT
+    return key
+
+
 def ncu_traffic(workload, occ=None, skip=None):
     """DRAM bytes per launch (read + write) from the committed ncu summary, or None."""
     d = ncu_summary(workload, occ, skip)
@@ -772,10 +785,7 @@ def run_multiscale(args):
     kernels, inst, dram = {}, 0.0, 0.0
     for k in sorted(set(lev)):
         rays_k = sum(v.W * v.H for v, l in zip(views, lev) if l == k)
-        occ_k = "nested" if args.engine == "nested" else occupancy_key(args.occupancy, tuned.get(str(k)))
-        if occ_k is None and tuned.get(str(k), {}).get("tile") in ((8, 4), [8, 4]) and \
-                tuned[str(k)].get("schedule") == 2:  # LFP_SCHED_PERSISTENT
-            occ_k = "nested"
+        occ_k = level_config_key(args.engine, args.occupancy, tuned.get(str(k)))
         kernels[str(k)] = (f"render_stream_kernel ({occ_k} blocks/SM)" if occ_k not in (None, "nested") else
                            "render_kernel (loop nest)")
         c = summ.get(str(k), {}).get("by_occupancy", {}).get(occ_k or "", {})

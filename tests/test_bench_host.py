@@ -1,5 +1,6 @@
 """Host logic that needs no GPU: in bench.py, which committed ncu summary a
-launch may use (source hash, register budget), the issue roofline arithmetic
+launch may use (source hash, register budget, skip level, multi-scale level
+configuration), the issue roofline arithmetic
 and the algorithmic-bytes model of the fetch counters; in the binding, the
 autotuner cache's key and file."""
 import json
@@ -45,6 +46,28 @@ def test_summary_per_register_budget(tmp_path, monkeypatch):
     assert bench.ncu_summary("batched", None) == {}
 
 
+def test_summary_needs_the_skip_level_it_was_taken_at(tmp_path, monkeypatch):
+    """Counts depend on the block side the walk skipped with: a summary is
+    used only for a launch at the same skip level (one per multi-scale level)."""
+    _profiles(tmp_path, monkeypatch, "room", {"source_sha": "abc", "skip_block": 4, "warp_inst_per_launch": 10,
+                                               "dram_bytes_per_launch": 5})
+    assert bench.ncu_traffic("room", "8", 4) == 5.0
+    assert bench.ncu_traffic("room", "8", 8) is None
+    assert bench.ncu_traffic("room", "8") is None
+    _profiles(tmp_path, monkeypatch, "multiscale", {"source_sha": "abc", "skip_block": [4, 8, 16], "levels": {}})
+    assert bench.ncu_summary("multiscale", skip=[4, 8, 16]) != {}
+    assert bench.ncu_summary("multiscale", skip=[4, 8, 32]) == {}
+
+
+def test_level_config_key():
+    assert bench.level_config_key("nested", "auto", None) == "nested"
+    assert bench.level_config_key("auto", "9", None) == "9"
+    assert bench.level_config_key("auto", "auto", {"engine": 1, "occupancy": 2}) == "9"
+    assert bench.level_config_key("auto", "auto", {"engine": 2, "tile": [8, 4], "schedule": 2}) == "nested"
+    assert bench.level_config_key("auto", "auto", {"engine": 2, "tile": [16, 8], "schedule": 2}) is None
+    assert bench.level_config_key("auto", "auto", {"engine": 2, "tile": [8, 4], "schedule": 1}) is None
+
+
 def test_issue_roofline_arithmetic(tmp_path, monkeypatch):
     # 1258.56 G warp instructions in one second at 2070 MHz on 152 SMs = 100 %
     _profiles(tmp_path, monkeypatch, "room", {"source_sha": "abc", "warp_inst_per_launch": 1258.56e6,
@@ -79,6 +102,7 @@ def test_committed_summaries_parse():
     for f in files:
         d = json.load(open(f))
         assert "source_sha" in d, f
+        assert isinstance(d.get("skip_block"), (int, list)), f
         entries = list(d.get("by_occupancy", {}).values())
         for lv in d.get("levels", {}).values():
             entries += list(lv["by_occupancy"].values())
