@@ -193,7 +193,8 @@ enum { LFP_OCC_AUTO = 0, LFP_OCC_8 = 1, LFP_OCC_9 = 2 };
 lfp_status lfp_create_grid(const lfp_grid_desc* desc, lfp_grid** out);
 
 /* Upload maps for probes [first_probe, first_probe + count) and rebuild their
- * low-resolution min/max maps (Sec. 5.1) at every skip level. Host planes are copied before the
+ * low-resolution min/max maps (Sec. 5.1) at every skip level and the least
+ * distance of each quadrant of their maps (where a segment's walk starts). Host planes are copied before the
  * call returns only if the stream is synchronous; otherwise they must stay
  * valid until the stream has run the copy. Errors: INVALID_ARG, OOM, CUDA. */
 lfp_status lfp_upload_probes(lfp_grid* grid, int first_probe, int count,
@@ -298,9 +299,10 @@ lfp_status lfp_set_radiance(lfp_grid* grid, const float* dev_radiance_f32, void*
  * some ray reached max_steps, else LFP_OK. */
 lfp_status lfp_check_flags(lfp_grid* grid, void* cuda_stream);
 
-/* Device bytes the grid's probe storage takes for a descriptor (maps and
- * the min/max maps of every skip level), the byte accounting of Sec. 6
- * (memory efficient representation). */
+/* Device bytes the grid's probe storage takes for a descriptor (maps, the
+ * min/max maps of every skip level, and per probe the least distance of
+ * each quadrant of its map, 16 B), the byte accounting of Sec. 6 (memory
+ * efficient representation). */
 lfp_status lfp_grid_bytes(const lfp_grid_desc* desc, unsigned long long* bytes);
 
 /* Skip levels (Sec. 5.1 hierarchical tracing; the paper uses one
