@@ -265,10 +265,9 @@ __device__ __forceinline__ void seg_start(const GridDev& g, Lane& L) {
         (void)unused;
     }
     // the walk starts where the ray first reaches the least distance of the
-    // segment's map quadrant (segment_start; the nearest-probe traversal,
-    // whose segments gain less than the set-up costs, starts at u = 0)
-    float us = 0.0f;
-    if (!NEAREST) {
+    // segment's map quadrant (segment_start)
+    float us;
+    {
         bool walk;
         us = segment_start(s, __ldg(g.qmin + (size_t)L.probe * 4 + quad), walk);
         if (!walk) {
@@ -648,10 +647,9 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
 
         // the transitions run again while a lane's new segment ended at its
         // set-up (nearer than its quadrant's least distance), so such lanes
-        // reach their next segment in the same round (one pass for the
-        // nearest-probe traversal, whose segments always walk)
+        // reach their next segment in the same round
 #pragma unroll 1
-        for (int pass = 0; pass < (NEAREST ? 1 : kChainPasses); ++pass) {
+        for (int pass = 0; pass < kChainPasses; ++pass) {
             if (L.mode == kSegEnd) {  // MISS on this segment: next segment, or the probe is a MISS
                 if (CI(kSegFinal)) {
                     if (NEAREST) {  // a MISS falls through to the next probe too
@@ -706,7 +704,7 @@ __global__ void __launch_bounds__(kStreamThreads, kMinBlocks[OCC]) render_stream
                 L.mode = kSegStart;
             }
             if (L.mode == kSegStart) seg_start<NEAREST>(g, L);  // kWalk, or kSegEnd for a segment nearer than its quadrant
-            if (NEAREST || !__any_sync(kFull, L.mode == kSegEnd)) break;
+            if (!__any_sync(kFull, L.mode == kSegEnd)) break;
         }
 
         // ---- walk phase: one texel visit per walking lane per step, until

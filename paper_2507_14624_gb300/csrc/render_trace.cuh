@@ -198,7 +198,7 @@ __device__ __forceinline__ float fine_start(const Seg& s, float d2, float u0, fl
     return fminf(fmaxf(us, u0), u1);
 }
 
-// Where a segment's low-resolution walk can start (grid traversal). dq is
+// Where a segment's low-resolution walk can start. dq is
 // the least distance stored in the segment's quadrant of the map: while the
 // ray's radial distance stays below dq it is in front of every texel there,
 // so the walk starts where it first reaches dq (the fine_start estimate over
@@ -295,8 +295,8 @@ __device__ bool trace_segment(const GridDev& g, const Seg& s, int probe, Decisio
         return fine_walk<NRMF, COUNT>(g, s, pbase, 0.0f, s.u_end, s.A0, 1.0f, s.lo[0], s.lo[1], s.hi[0], s.hi[1],
                                       out, st, step_limited);
     const float* mip = g.mip + (size_t)probe * 2 * M * M;  // min plane; the max plane follows it
-    float u = 0.0f;
-    if (!g.nearest_probes) {
+    float u;
+    {
         bool walk;
         const int quad = (s.lo[0] > 0 ? 1 : 0) | (s.lo[1] > 0 ? 2 : 0);
         u = segment_start(s, __ldg(g.qmin + (size_t)probe * 4 + quad), walk);
