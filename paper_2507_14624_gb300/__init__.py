@@ -361,24 +361,39 @@ class ProbeHierarchy:
         o.counters = out["counters"].data_ptr() if counters else None
         return out, o
 
-    def render(self, views, aux=True, hit_texel=False, counters=False, engine=0, occupancy=0, stream=None):
-        """Like ProbeGrid.render; `probe` indexes the probes of each view's level."""
+    def autotune(self, views, stream=None) -> dict:
+        """Pick each level's launch configuration and skip level on the views
+        that level renders (ProbeGrid.autotune per level); returns {level: pick}."""
+        lev = self.level_of(views)
+        picks = {}
+        for k, g in enumerate(self.grids):
+            mine = [v for v, l in zip(views, lev) if l == k]
+            if mine:
+                picks[k] = g.autotune(mine, stream=stream)
+        return picks
+
+    def render(self, views, aux=True, hit_texel=False, counters=False, engine=0, occupancy=0, skip_block=0,
+               stream=None):
+        """Like ProbeGrid.render; `probe` indexes the probes of each view's
+        level. A nonzero skip_block must be a skip level of every level that
+        renders a view (0: each level's default)."""
         arr, n, total = make_views(views)
         out, o = self._outputs(total, aux, hit_texel, counters)
         opts = lfp.lfp_render_opts()
         opts.engine = engine
         opts.occupancy = occupancy
+        opts.skip_block = skip_block
         lfp.lfp_render_levels(self.handles, arr, n, o, opts, _stream_handle(stream))
         return out
 
-    def render_graph(self, views, aux=False, engine=0, occupancy=0, stream=None):
+    def render_graph(self, views, aux=False, engine=0, occupancy=0, skip_block=0, stream=None):
         """One hierarchy render captured in a CUDA graph (outputs reused);
-        engine / occupancy as in render (0: each level's default)."""
+        engine / occupancy / skip_block as in render (0: each level's default)."""
         import torch
         s = torch.cuda.Stream() if stream is None else stream
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            out = self.render(views, aux=aux, engine=engine, occupancy=occupancy, stream=s)
+            out = self.render(views, aux=aux, engine=engine, occupancy=occupancy, skip_block=skip_block, stream=s)
         torch.cuda.current_stream().wait_stream(s)
         arr, n, total = make_views(views)
         o = lfp.lfp_outputs()
@@ -388,6 +403,7 @@ class ProbeHierarchy:
         opts = lfp.lfp_render_opts()
         opts.engine = engine
         opts.occupancy = occupancy
+        opts.skip_block = skip_block
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=s):
             lfp.lfp_render_levels(self.handles, arr, n, o, opts, _stream_handle(s))

@@ -152,3 +152,28 @@ def test_flat_march_matches_every_skip_level(name):
             a = grid.render(views, hit_texel=True, skip_block=k, engine=eng)
             same = (a["cls"] == flat["cls"]) & (a["texel"] == flat["texel"])
             assert same.float().mean().item() >= 0.9999, (k, eng)
+
+
+def test_hierarchy_autotune_picks_per_level():
+    """ProbeHierarchy.autotune tunes each level on the views it renders; the
+    picks become the levels' defaults and the images keep their decisions."""
+    import paper_2507_14624_gb300 as lfpk
+    coarse = synth.Grid(2, 2, 2, 1.0, 64, 16)
+    fine = synth.Grid(2, 2, 2, 0.5, 96, 8, (0.25, 0.25, 0.25))
+    sc = synth.make_scene(coarse, 6, 2, [1.0], seed=5)
+    grids = []
+    for g in (coarse, fine):
+        pg = lfpk.ProbeGrid(g)
+        pg.upload(*synth.level_scene(sc, g).probe_maps())
+        grids.append(pg)
+    h = lfpk.ProbeHierarchy(grids)
+    views = [synth.random_view(sc, 90 + s, 64, 48, 70.0) for s in range(6)]
+    before = h.render(views, hit_texel=True)
+    picks = h.autotune(views)
+    lev = h.level_of(views)
+    assert set(picks) == set(lev)
+    for k, p in picks.items():
+        assert p["skip_block"] in grids[k].skip_blocks, (k, p)
+    after = h.render(views, hit_texel=True)
+    same = (before["cls"] == after["cls"]) & (before["texel"] == after["texel"])
+    assert same.float().mean().item() >= 0.9999
