@@ -232,8 +232,8 @@ bool valid_tile(int w, int h) {
 lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const OutDev& out,
                        const lfp_render_opts* opts, cudaStream_t s, unsigned* queue = nullptr) {
     // A launch alone on the GPU ends with a tail where warps run dry while
-    // others still hold rays; the streaming engine hands its last two tiles
-    // per warp out as half tiles to even it out. Overlapping launches fill
+    // others still hold rays; the streaming engine hands its last tile per
+    // warp out as two half tiles to even it out. Overlapping launches fill
     // each other's tails, so there the split would only add queue traffic.
     const bool overlapped = queue != nullptr;
     if (!queue) queue = g->tile_counter;  // the persistent launches' work-queue head
@@ -282,7 +282,7 @@ lfp_status render_impl(lfp_grid* g, const lfp_view* views, int n_views, const Ou
             }
             vb.total_tiles = (int)tiles;
             int blocks = (int)std::min<long long>(g->stream_blocks[occ], (tiles + 3) / 4);
-            vb.tail_tiles = overlapped ? 0 : 2 * blocks * (kStreamThreadsPerBlock / 32);
+            vb.tail_tiles = overlapped ? 0 : blocks * (kStreamThreadsPerBlock / 32);
             LFP_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
             LFP_CUDA(launch_render_stream(gd, g->desc.radiance_fmt, g->desc.normal_fmt, vb, out, queue,
                                           blocks, occ, s));
