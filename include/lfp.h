@@ -183,7 +183,8 @@ typedef struct {
                        results, different speed per workload */
     int skip_block; /* side, in full-resolution texels, of the min/max
                        blocks the walk skips over: one of lfp_skip_blocks,
-                       or 0 for the grid's default. Both engines. */
+                       or 0 for the grid's default. Both engines; identical
+                       decisions, different speed per workload */
 } lfp_render_opts;
 enum { LFP_OCC_AUTO = 0, LFP_OCC_8 = 1, LFP_OCC_9 = 2 };
 
@@ -194,9 +195,10 @@ lfp_status lfp_create_grid(const lfp_grid_desc* desc, lfp_grid** out);
 
 /* Upload maps for probes [first_probe, first_probe + count) and rebuild their
  * low-resolution min/max maps (Sec. 5.1) at every skip level and the least
- * distance of each quadrant of their maps (where a segment's walk starts). Host planes are copied before the
- * call returns only if the stream is synchronous; otherwise they must stay
- * valid until the stream has run the copy. Errors: INVALID_ARG, OOM, CUDA. */
+ * distance of each quadrant of their maps (where a segment's walk starts).
+ * Host planes are copied before the call returns only if the stream is
+ * synchronous; otherwise they must stay valid until the stream has run the
+ * copy. Errors: INVALID_ARG, OOM, CUDA. */
 lfp_status lfp_upload_probes(lfp_grid* grid, int first_probe, int count,
                              const lfp_probe_planes* planes, void* cuda_stream);
 
