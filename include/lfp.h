@@ -183,8 +183,9 @@ typedef struct {
                        results, different speed per workload */
     int skip_block; /* side, in full-resolution texels, of the min/max
                        blocks the walk skips over: one of lfp_skip_blocks,
-                       or 0 for the grid's default. Both engines; identical
-                       decisions, different speed per workload */
+                       or 0 for the grid's default. Both engines; the same
+                       decisions up to near-ties, different speed per
+                       workload */
 } lfp_render_opts;
 enum { LFP_OCC_AUTO = 0, LFP_OCC_8 = 1, LFP_OCC_9 = 2 };
 
